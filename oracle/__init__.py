@@ -1,0 +1,161 @@
+"""CPU oracle of the PLUGIN bandwidth selector (Algorithm 1, Steps I-VII; Eqs. 6-7).
+
+TEST INFRASTRUCTURE ONLY.  Only ``tests/``, ``__graft_entry__.smoke()`` and the
+CPU-baseline leg of ``bench.py`` may import this package.  The product library
+(the CUDA path behind the C ABI) never imports, links or calls it, and the two
+share no code: this package is plain C compiled with gcc plus a ctypes shim.
+
+Precision: IEEE binary64 throughout, compensated (Neumaier) sums; a long double
+brute force (``plugin_ld`` / ``psi_ld``) for tiny n.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "kde_oracle.c")
+_LIB = os.path.join(_HERE, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+OK, ERR_INVALID, ERR_DEGENERATE, ERR_DOMAIN = 0, 1, 2, 3
+FORM_FULL, FORM_SYMMETRIC = 0, 1
+
+
+class Result(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_double) for k in
+                ("mean", "sigma", "psi8", "g1", "psi6", "g2", "psi4", "h")] + [("status", ctypes.c_int)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class ResultLD(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_longdouble) for k in
+                ("mean", "sigma", "psi8", "g1", "psi6", "g2", "psi4", "h")] + [("status", ctypes.c_int)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+def build(force: bool = False) -> str:
+    """Compile ``liboracle.so`` with gcc (no GPU, no CUDA)."""
+    with _lock:
+        if (not force and os.path.exists(_LIB)
+                and os.path.getmtime(_LIB) >= max(os.path.getmtime(_SRC),
+                                                  os.path.getmtime(os.path.join(_HERE, "kde_oracle.h")))):
+            return _LIB
+        tmp = _LIB + f".tmp{os.getpid()}"
+        subprocess.run(["gcc", "-O2", "-fPIC", "-shared", "-std=c11", "-fno-fast-math",
+                        "-ffp-contract=off", "-Wall", "-o", tmp, _SRC, "-lm", "-lpthread"],
+                       check=True)
+        os.replace(tmp, _LIB)
+        return _LIB
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        build()
+        lib = ctypes.CDLL(_LIB)
+        d, i64, ip = ctypes.c_double, ctypes.c_int64, ctypes.c_int
+        dp = ctypes.POINTER(ctypes.c_double)
+        lib.oracle_moments.argtypes = [dp, i64, dp, dp]
+        lib.oracle_kernel_deriv.argtypes = [ip, d]
+        lib.oracle_kernel_deriv.restype = d
+        lib.oracle_psi.argtypes = [dp, i64, ip, d, ip, ip, dp]
+        lib.oracle_psi_block.argtypes = [dp, i64, i64, i64, i64, i64, ip, d, dp, dp]
+        lib.oracle_plugin.argtypes = [dp, i64, ip, ip, ctypes.POINTER(Result)]
+        lib.oracle_plugin_ld.argtypes = [dp, i64, ctypes.POINTER(ResultLD)]
+        lib.oracle_psi_ld.argtypes = [dp, i64, ip, ctypes.c_longdouble,
+                                      ctypes.POINTER(ctypes.c_longdouble)]
+        lib.oracle_long_double_mantissa_bits.restype = ip
+        _lib = lib
+    return _lib
+
+
+def default_threads() -> int:
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:  # pragma: no cover
+        return os.cpu_count() or 1
+
+
+def _arr(x) -> np.ndarray:
+    return np.ascontiguousarray(np.asarray(x, dtype=np.float64))
+
+
+def _ptr(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def moments(x):
+    """Step I: (mean, unbiased variance)."""
+    a = _arr(x)
+    m, v = ctypes.c_double(), ctypes.c_double()
+    st = _load().oracle_moments(_ptr(a), a.size, ctypes.byref(m), ctypes.byref(v))
+    if st != OK:
+        raise ValueError(f"oracle_moments status {st}")
+    return m.value, v.value
+
+
+def kernel_deriv(r: int, u: float) -> float:
+    """K^(r)(u), r in {4, 6} (Algorithm 1, Steps IV and VI)."""
+    return _load().oracle_kernel_deriv(int(r), float(u))
+
+
+def psi(x, r: int, g: float, form: int = FORM_SYMMETRIC, threads: int | None = None) -> float:
+    """psi_r(g) = n^-2 g^-(r+1) sum_i sum_j K^(r)((X_i - X_j)/g)."""
+    a = _arr(x)
+    out = ctypes.c_double()
+    st = _load().oracle_psi(_ptr(a), a.size, int(r), float(g), int(form),
+                            int(threads or default_threads()), ctypes.byref(out))
+    if st != OK:
+        raise ValueError(f"oracle_psi status {st}")
+    return out.value
+
+
+def psi_block(x, i0: int, i1: int, j0: int, j1: int, r: int, g: float):
+    """(sum, sum of |terms|) of K^(r)((X_i - X_j)/g) over i in [i0,i1), j in [j0,j1), i < j."""
+    a = _arr(x)
+    s, t = ctypes.c_double(), ctypes.c_double()
+    st = _load().oracle_psi_block(_ptr(a), a.size, i0, i1, j0, j1, int(r), float(g),
+                                  ctypes.byref(s), ctypes.byref(t))
+    if st != OK:
+        raise ValueError(f"oracle_psi_block status {st}")
+    return s.value, t.value
+
+
+def plugin(x, form: int = FORM_SYMMETRIC, threads: int | None = None) -> dict:
+    """Algorithm 1, Steps I-VII; returns the dict of all intermediate scalars."""
+    a = _arr(x)
+    res = Result()
+    _load().oracle_plugin(_ptr(a), a.size, int(form), int(threads or default_threads()),
+                          ctypes.byref(res))
+    return res.as_dict()
+
+
+def plugin_ld(x) -> dict:
+    """Algorithm 1 in long double by brute force (full double loop)."""
+    a = _arr(x)
+    res = ResultLD()
+    _load().oracle_plugin_ld(_ptr(a), a.size, ctypes.byref(res))
+    return res.as_dict()
+
+
+def psi_ld(x, r: int, g: float) -> float:
+    a = _arr(x)
+    out = ctypes.c_longdouble()
+    st = _load().oracle_psi_ld(_ptr(a), a.size, int(r), ctypes.c_longdouble(g), ctypes.byref(out))
+    if st != OK:
+        raise ValueError(f"oracle_psi_ld status {st}")
+    return out.value
+
+
+def long_double_bits() -> int:
+    return _load().oracle_long_double_mantissa_bits()

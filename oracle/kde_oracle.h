@@ -1,0 +1,72 @@
+/*
+ * kde_oracle.h -- plain, slow, obviously correct CPU reference for the PLUGIN
+ * bandwidth selector (Algorithm 1 of Gramacki, Sawerwain & Gramacki,
+ * "FPGA-Based Bandwidth Selection for Kernel Density Estimation Using High
+ * Level Synthesis Approach").
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing in the product path may include, link or
+ * call this library; only the tests, the smoke check and the benchmark's CPU
+ * baseline leg use it.  It shares no code with the CUDA library.
+ *
+ * Everything is IEEE binary64 except the *_ld brute-force entry points, which
+ * use long double (binary128 on aarch64, x87 80-bit on x86-64).
+ */
+#ifndef KDE_ORACLE_H
+#define KDE_ORACLE_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+    ORACLE_OK = 0,
+    ORACLE_ERR_INVALID = 1,     /* null pointer, n < 2, r not in {4, 6}, g <= 0 or not finite */
+    ORACLE_ERR_DEGENERATE = 2,  /* sigma == 0 */
+    ORACLE_ERR_DOMAIN = 3       /* psi6 >= 0 (g2 undefined) or psi4 <= 0 (h undefined) */
+};
+
+/* How the O(n^2) double sum of Steps IV and VI is taken. */
+enum {
+    ORACLE_FORM_FULL = 0,       /* sum over all i and all j, as printed in Steps IV / VI */
+    ORACLE_FORM_SYMMETRIC = 1   /* 2 * sum_{i<j} + n K^(r)(0), Eqs. (6) and (7) */
+};
+
+typedef struct {
+    double mean, sigma, psi8, g1, psi6, g2, psi4, h;
+    int status;
+} oracle_result;
+
+typedef struct {
+    long double mean, sigma, psi8, g1, psi6, g2, psi4, h;
+    int status;
+} oracle_result_ld;
+
+/* Step I: mean and unbiased variance (divisor n-1), two-pass. */
+int oracle_moments(const double* x, int64_t n, double* mean, double* var);
+
+/* K^(r)(u) for r in {4, 6}, the printed Hermite forms of Steps IV and VI. */
+double oracle_kernel_deriv(int r, double u);
+
+/* psi_r(g) = n^-2 g^-(r+1) sum_i sum_j K^(r)((X_i - X_j)/g), Steps IV / VI. */
+int oracle_psi(const double* x, int64_t n, int r, double g, int form, int nthreads,
+               double* psi);
+
+/* Unnormalised block sum over i in [i0,i1), j in [j0,j1) with i < j of
+ * K^(r)((X_i - X_j)/g); also the sum of absolute values of the same terms. */
+int oracle_psi_block(const double* x, int64_t n, int64_t i0, int64_t i1, int64_t j0,
+                     int64_t j1, int r, double g, double* sum, double* abs_sum);
+
+/* The whole of Algorithm 1, Steps I-VII. */
+int oracle_plugin(const double* x, int64_t n, int form, int nthreads, oracle_result* out);
+
+/* Brute force in long double: full double loop, plain summation. */
+int oracle_plugin_ld(const double* x, int64_t n, oracle_result_ld* out);
+int oracle_psi_ld(const double* x, int64_t n, int r, long double g, long double* psi);
+int oracle_long_double_mantissa_bits(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif
