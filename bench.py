@@ -1,0 +1,352 @@
+"""Benchmark of the PLUGIN hot path: psi6 + psi4 pair evaluations per second.
+
+A step is one whole PLUGIN run (Algorithm 1, Steps I-VII) on one sample through
+the C ABI: moments, psi6(g1) over n(n-1)/2 unique pairs, g2, psi4(g2) over
+n(n-1)/2 pairs, h.  The workload is n = 65536 values of the bimodal mixture
+0.5 N(-1, 0.5^2) + 0.5 N(1, 0.5^2) shifted by +1e4 (seeded, synthetic).
+
+  value     FP32 pair path, input resident in HBM, device time per step (CUDA
+            events on the launching stream); L2 flushed between steps.
+  e2e       same metric through the same call with pinned HOST input and a host
+            result struct: H2D copy, all kernels, D2H copy, synchronize.
+  roofline  the pair kernel (r = 6), timed live by events recorded around it
+            inside the captured graph, against the FP32-issue / MUFU ALU bound.
+  fp64      the all-binary64 GPU path on the same workload.
+  cpu_baseline  the CPU oracle on this host's cores, one full run.
+
+`--impl reference` times the CPU oracle instead (the reference arm).
+Under torchrun (N > 1) every rank runs the workload on its own GPU (replicas);
+value is the sum over ranks and the time the max over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "psi4+psi6 pair-evals/s"
+UNIT = "pair-evals/s"
+N_DEFAULT = 65536
+WORKLOAD = "plugin-bimodal-n65536"
+
+
+def pairs_per_step(n: int) -> int:
+    return 2 * (n * (n - 1) // 2)
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--n", type=int, default=N_DEFAULT)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp64", action="store_true")
+    return ap.parse_args()
+
+
+def dist_setup():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("gloo")
+    return ws, rank, local
+
+
+def dist_max(v: float, ws: int) -> float:
+    if ws == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([v], dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(ws: int):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def workload(n: int):
+    import synthdata
+    return synthdata.bimodal_offset(n=n)
+
+
+def rel_errors(res, ref):
+    return {f: abs(res[f] - ref[f]) / abs(ref[f]) for f in ("psi6", "psi4", "h")}
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle sampling while the timed region runs."""
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu: int):
+        self.gpu = gpu
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_gpu{gpu}.csv")
+
+    def __enter__(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.QUERY}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.f.close()
+
+    def summary(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        rows = []
+        for line in open(self.path):
+            c = [v.strip() for v in line.split(",")]
+            if len(c) >= 9 and c[1].isdigit():
+                rows.append(c)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [int(r[1]) for r in rows]
+        mx = max(int(r[2]) for r in rows)
+        loaded = [v for v in sm if v > 0.5 * mx] or sm
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(loaded), "sm_max_mhz": mx, "reasons": reasons,
+                "samples": len(rows)}
+
+
+# Instructions per unique pair of the binary32 pair kernel (all issue on the
+# FP32/INT pipes, no MUFU):
+#   FADD  d = y_i - y_j (exact on the per-sample grid)
+#   FMUL  v = d^2 ;  FMNMX  clamp of v
+#   FFMA + FADD + 2 FFMA   k = round(t), f = t - k for t = -u^2/(2 ln 2)
+#   8 FFMA   degree-8 polynomial for 2^f
+#   SHL + IADD   2^k into the exponent field
+#   r/2 FFMA   Horner for He_r on v (3 for He_6, 2 for He_4)
+#   FMUL   term ;  4 FADD   Kahan-compensated accumulation
+ISSUE_PER_PAIR = {6: 25, 4: 24}
+
+
+def alu_peak(r: int, sms: int, f_mhz: float):
+    """Pair-evaluation roofline of the r-th pair kernel from unit counts and clock.
+
+    Each SM issues one warp instruction per clock in each of its 4 sub-partitions
+    (128 lane slots per clock); every instruction of the per-pair sequence takes
+    a slot, so the bound is 128 / ISSUE_PER_PAIR[r] pairs per clock per SM.
+    """
+    per_clk = 128.0 / ISSUE_PER_PAIR[r]
+    return {"pairs_per_s": sms * f_mhz * 1e6 * per_clk, "pairs_per_clk_sm": per_clk}
+
+
+def run_reference(args, ws, rank):
+    if rank != 0:
+        return
+    import numpy as np
+
+    import oracle
+    x = workload(args.n)
+    cores = oracle.default_threads()
+    for _ in range(args.warmup):
+        oracle.plugin(x, threads=cores)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        oracle.plugin(x, threads=cores)
+        times.append(time.perf_counter() - t0)
+    total = sum(times)
+    value = args.steps * pairs_per_step(args.n) / total
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": WORKLOAD, "n": args.n, "l2": "n/a (CPU)"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": f"full PLUGIN run per step on n={args.n} (symmetric form, "
+                                   f"{pairs_per_step(args.n)} pair-evals)"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+
+
+def run_ours(args, ws, rank, local):
+    import numpy as np
+    import torch
+
+    import paper_1505_02100_gb300 as kde
+    from paper_1505_02100_gb300 import build as kbuild
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if rank == 0 and not kbuild.up_to_date():
+        kbuild.build()
+    barrier(ws)
+    kde.load()
+    n = args.n
+    x = workload(n)
+    xd = torch.tensor(x, dtype=torch.float64, device=dev)
+    out = torch.empty(kde.RESULT_BYTES // 8, dtype=torch.float64, device=dev)
+    stream = torch.cuda.Stream(device=dev)
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)   # > 129 MB L2
+
+    def timed(prec, steps, warmup, profile):
+        kde.kde_profile_enable(profile)
+        for _ in range(warmup):
+            kde.kde_plugin_h(xd, prec, out=out, stream=stream)
+        stream.synchronize()
+        step_ms, k6, k4 = [], [], []
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(steps)]
+        barrier(ws)
+        torch.cuda.synchronize()
+        for i in range(steps):
+            with torch.cuda.stream(stream):
+                flush.zero_()
+            ev[i][0].record(stream)
+            kde.kde_plugin_h(xd, prec, out=out, stream=stream)
+            ev[i][1].record(stream)
+            if profile:
+                t = kde.kde_profile_last(stream)
+                k6.append(t["pairs6"])
+                k4.append(t["pairs4"])
+        torch.cuda.synchronize()
+        barrier(ws)
+        step_ms = [a.elapsed_time(b) for a, b in ev]
+        kde.kde_profile_enable(False)
+        return step_ms, k6, k4
+
+    # FP32 pair path: the headline
+    with ClockSampler(local) as clk:
+        step_ms, k6, k4 = timed(kde.KDE_FP32, args.steps, args.warmup, True)
+    clocks = clk.summary()
+    total_s = dist_max(sum(step_ms) / 1e3, ws)
+    res32 = kde.kde_plugin_h(xd, kde.KDE_FP32)
+    value = ws * args.steps * pairs_per_step(n) / total_s
+
+    # end to end through the C ABI: pinned host input, host result, synchronous
+    xh = torch.tensor(x, dtype=torch.float64).pin_memory()
+    for _ in range(args.warmup):
+        kde.kde_plugin_h(xh, kde.KDE_FP32, stream=stream)
+    e2e_t = []
+    for _ in range(args.steps):
+        with torch.cuda.stream(stream):
+            flush.zero_()
+        stream.synchronize()
+        t0 = time.perf_counter()
+        r = kde.kde_plugin_h(xh, kde.KDE_FP32, stream=stream)
+        e2e_t.append(time.perf_counter() - t0)
+        assert r["status"] == 0
+    e2e_total = dist_max(sum(e2e_t), ws)
+    e2e_value = ws * args.steps * pairs_per_step(n) / e2e_total
+
+    # FP64 path
+    fp64 = None
+    if not args.no_fp64:
+        k = max(2, args.steps // 4)
+        ms64, k6_64, k4_64 = timed(kde.KDE_FP64, k, 1, True)
+        res64 = kde.kde_plugin_h(xd, kde.KDE_FP64)
+        t64 = dist_max(sum(ms64) / 1e3, ws)
+        fp64 = {"value": ws * k * pairs_per_step(n) / t64, "unit": UNIT,
+                "ms_per_step": 1e3 * t64 / k, "steps": k,
+                "pairs6_ms": statistics.mean(k6_64), "pairs4_ms": statistics.mean(k4_64),
+                "h": res64["h"]}
+
+    if rank != 0:
+        return
+    with ClockSampler(local) as pclk:
+        rates = kde.kde_probe_pipe_rates()
+    probe_mhz = pclk.summary()["sm_mhz"] or 2070.0
+    sms = int(rates["sms"])
+    rates_clk = {"fp32_fma_lanes_per_clk_sm": rates["fp32_fma_lanes_per_s_sm"] / (probe_mhz * 1e6),
+                 "mufu_ex2_per_clk_sm": rates["mufu_ex2_per_s_sm"] / (probe_mhz * 1e6),
+                 "fp64_fma_lanes_per_clk_sm": rates["fp64_fma_lanes_per_s_sm"] / (probe_mhz * 1e6),
+                 "probe_sm_mhz": probe_mhz}
+    peak = alu_peak(6, sms, 2070.0)
+    peak4 = alu_peak(4, sms, 2070.0)
+    pairs = n * (n - 1) // 2
+    k6_ms = statistics.mean(k6)
+    achieved = pairs / (k6_ms / 1e3)
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * total_s / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n": n, "distribution": "0.5N(-1,0.5^2)+0.5N(1,0.5^2)+1e4",
+                   "precision": "fp32 pair terms, fp64 moments/reductions/scalars",
+                   "l2": "flushed between steps (512 MiB write outside the timed events)",
+                   "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU"},
+        "gpu_launches": 4 * args.steps,
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 8 * n,
+                "d2h_bytes_per_step": kde.RESULT_BYTES},
+        "roofline": {"bound": "alu", "kernel": "pairs_kernel r=6 (Step IV)",
+                     "achieved": achieved / 1e9, "peak": peak["pairs_per_s"] / 1e9, "unit": "Gpair/s",
+                     "frac": achieved / peak["pairs_per_s"], "traffic": None,
+                     "peak_basis": f"{sms} SMs x 2070 MHz x 128 issue slots / {ISSUE_PER_PAIR[6]} "
+                                   f"instructions per pair = {peak['pairs_per_clk_sm']:.2f} pairs/clk/SM",
+                     "pairs4_kernel": {"ms": statistics.mean(k4),
+                                       "achieved": pairs / (statistics.mean(k4) / 1e3) / 1e9,
+                                       "peak": peak4["pairs_per_s"] / 1e9,
+                                       "frac": pairs / (statistics.mean(k4) / 1e3) / peak4["pairs_per_s"]},
+                     "pairs6_ms": k6_ms,
+                     "frac_at_measured_clock": achieved / (peak["pairs_per_s"] * (clocks["sm_mhz"] or 2070.0) / 2070.0),
+                     "probe": rates_clk},
+        "clocks": clocks,
+        "accuracy": {"fp32_status": res32["status"], "h_fp32": res32["h"]},
+    }
+    if fp64:
+        line["fp64"] = fp64
+        line["fp32_over_fp64"] = value / fp64["value"]
+    if not args.no_cpu_baseline:
+        import oracle
+        cores = oracle.default_threads()
+        t0 = time.perf_counter()
+        ref = oracle.plugin(x, threads=cores)
+        dt = time.perf_counter() - t0
+        line["cpu_baseline"] = {"value": pairs_per_step(n) / dt, "unit": UNIT, "cores": cores,
+                                "kind": "oracle",
+                                "sample": f"one full PLUGIN run on the same n={n} sample "
+                                          f"({pairs_per_step(n)} pair-evals, {dt:.2f} s)"}
+        line["accuracy"]["rel_err_fp32_vs_oracle"] = rel_errors(res32, ref)
+        if fp64:
+            line["accuracy"]["rel_err_fp64_vs_oracle"] = rel_errors(res64, ref)
+    print(json.dumps(line))
+
+
+def main():
+    args = parse()
+    ws, rank, local = dist_setup()
+    if args.impl == "reference":
+        run_reference(args, ws, rank)
+    else:
+        run_ours(args, ws, rank, local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,215 @@
+/*
+ * kde.h -- C ABI of libkde, a GB300 (sm_103a) implementation of the two-stage
+ * direct plug-in (PLUGIN) bandwidth selector for univariate Gaussian kernel
+ * density estimation (Gramacki, Sawerwain & Gramacki, "FPGA-Based Bandwidth
+ * Selection for Kernel Density Estimation Using High Level Synthesis Approach",
+ * Algorithm 1 and Eqs. 1-8).
+ *
+ * Notation.  K = phi, the standard normal density (Eq. 2).  K^(r) is its r-th
+ * derivative; for even r, K^(r)(u) = He_r(u) phi(u) with He_r the probabilists'
+ * Hermite polynomial: He_4 = u^4 - 6u^2 + 3, He_6 = u^6 - 15u^4 + 45u^2 - 15
+ * (Algorithm 1, Steps IV and VI).
+ *
+ * Conventions shared by every entry point.
+ *  - All functions return a kde_status; none throws or aborts.  A non-OK return
+ *    leaves a thread-local message readable with kde_last_error().
+ *  - Pointers may be host or device memory unless stated otherwise; the library
+ *    asks the CUDA runtime which, copies host data itself, and never keeps a
+ *    caller pointer after the call returns (the server copies at submit).
+ *  - The caller owns every buffer it passes.  The library owns its own device
+ *    workspaces and frees them in kde_shutdown() or at process exit.
+ *  - `stream` is a cudaStream_t (NULL = the legacy default stream).  When every
+ *    output pointer is device memory the call only enqueues work on `stream`
+ *    and returns; the status words in the device outputs are then the result.
+ *    When an output is host memory the call waits for `stream` before it
+ *    returns.
+ *  - Precision: KDE_FP32 evaluates the O(n^2) pair terms in binary32 (exact
+ *    differences on a per-sample fixed grid, exp on the FMA pipe, compensated
+ *    per-thread sums) with sorting, moments, block and final sums and all
+ *    scalar steps in binary64; KDE_FP64 does everything in binary64.
+ *  - Every sample is sorted on the device first, so results do not depend on
+ *    the order of the input values (bitwise).
+ *  - psi values use the paper's normalisation n^-2 g^-(r+1) sum_i sum_j
+ *    K^(r)((X_i - X_j)/g), diagonal i = j included (Steps IV and VI).
+ *  - A pair evaluation is one unique unordered pair i < j (Eqs. 6-7 add the
+ *    diagonal analytically); kde_psi on n values does n(n-1)/2 of them.
+ */
+#ifndef KDE_H
+#define KDE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define KDE_API __attribute__((visibility("default")))
+#else
+#define KDE_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    KDE_OK = 0,
+    KDE_ERR_INVALID = 1,     /* null pointer, n < 2, r not in {4,6}, g <= 0 or not finite,
+                                non-finite data, or data whose range overflows the format */
+    KDE_ERR_DEGENERATE = 2,  /* sample standard deviation is zero (Step I) */
+    KDE_ERR_DOMAIN = 3,      /* psi6 >= 0 (g2 undefined, Step V) or psi4 <= 0 (h undefined,
+                                Step VII); fields after the failing step are NaN */
+    KDE_ERR_OOM = 4,         /* device memory could not be reserved */
+    KDE_ERR_CUDA = 5,        /* a CUDA runtime call failed; see kde_last_error() */
+    KDE_ERR_TIMEOUT = 6,     /* a bounded wait ran out (server poll) */
+    KDE_ERR_BUSY = 7         /* admission refused: request larger than the server's budget,
+                                or the server is shutting down */
+} kde_status;
+
+typedef enum {
+    KDE_FP32 = 0,            /* binary32 pair terms, binary64 elsewhere */
+    KDE_FP64 = 1             /* binary64 everywhere */
+} kde_precision;
+
+/* Every scalar of Algorithm 1 for one sample.  In a device-memory output the
+ * struct is written by the GPU; status is KDE_OK when all fields are valid. */
+typedef struct {
+    double mean;   /* sample mean (used only to centre the data) */
+    double sigma;  /* Step I: sqrt of the unbiased variance, divisor n-1 */
+    double psi8;   /* Step II: normal-scale psi8 = 105 / (32 sqrt(pi) sigma^9) */
+    double g1;     /* Step III: (-2 K^(6)(0) / (mu2 psi8 n))^(1/9) */
+    double psi6;   /* Step IV: psi6(g1), Eq. 6 */
+    double g2;     /* Step V: (-2 K^(4)(0) / (mu2 psi6 n))^(1/7) */
+    double psi4;   /* Step VI: psi4(g2), Eq. 7 */
+    double h;      /* Step VII: (R(K) / (mu2^2 psi4 n))^(1/5), in the units of x */
+    int32_t status;/* kde_status of this sample */
+    int32_t reserved;
+} kde_result;
+
+/*
+ * kde_psi -- the functional psi_r(g) of Steps IV / VI (Eqs. 6-7) for a given g.
+ *   x      n samples, binary64, host or device, contiguous.
+ *   n      number of samples, n >= 2.
+ *   r      derivative order, 4 or 6.
+ *   g      bandwidth > 0, in the units of x.
+ *   prec   KDE_FP32 or KDE_FP64.
+ *   out    one double, host or device: psi_r(g).  With a device `out` the call is
+ *          asynchronous and a failed run writes NaN there.
+ *   stream cudaStream_t or NULL.
+ * Errors: KDE_ERR_INVALID (arguments, non-finite data), KDE_ERR_OOM, KDE_ERR_CUDA.
+ */
+KDE_API kde_status kde_psi(const double* x, int64_t n, int r, double g, kde_precision prec,
+                   double* out, void* stream);
+
+/*
+ * kde_plugin_h -- Algorithm 1, Steps I-VII, for one sample: the bandwidth h and
+ * every intermediate scalar.  x: n binary64 values (host or device); out: one
+ * kde_result (host or device).  The steps run back to back on the device; no
+ * scalar returns to the host between them.
+ * Errors: as kde_psi, plus KDE_ERR_DEGENERATE and KDE_ERR_DOMAIN (also in
+ * out->status).
+ */
+KDE_API kde_status kde_plugin_h(const double* x, int64_t n, kde_precision prec, kde_result* out,
+                        void* stream);
+
+/* As kde_plugin_h for binary32 samples (the pair path is the same; the moments
+ * read the binary32 values and widen them to binary64). */
+KDE_API kde_status kde_plugin_h_f32(const float* x, int64_t n, kde_precision prec, kde_result* out,
+                            void* stream);
+
+/*
+ * kde_plugin_h_batch -- Algorithm 1 for m independent samples in one pass:
+ * one moments launch, one persistent psi6 launch and one persistent psi4 launch
+ * over a work-list of (sample, chunk of tile pairs) items, captured once in a
+ * CUDA graph per batch shape and replayed.
+ *   x_packed  all samples back to back, binary64, host or device.
+ *   offsets   m+1 int64 offsets into x_packed (HOST memory), offsets[0] = 0,
+ *             non-decreasing; sample k is x_packed[offsets[k] .. offsets[k+1]).
+ *   m         number of samples, m >= 1.
+ *   out       m kde_result, host or device.  A sample with n < 2 gets
+ *             KDE_ERR_INVALID in its own status; the others still run.
+ * Each sample's result is bitwise the same as kde_plugin_h on that sample alone
+ * (the tiling and the summation order depend only on its n).
+ */
+KDE_API kde_status kde_plugin_h_batch(const double* x_packed, const int64_t* offsets, int64_t m,
+                              kde_precision prec, kde_result* out, void* stream);
+
+/*
+ * kde_psi_slots -- verification view of kde_psi: the per-chunk partial sums the
+ * pair kernel writes before its final reduction.  The library first sorts the
+ * sample in increasing order (psi_r does not depend on the order); indices
+ * below refer to that sorted sample X_(1) <= ... <= X_(n).  Slot k holds the
+ * sum of He_r(u) exp(-u^2/2), u = (X_(i) - X_(j))/g, over the unique pairs i < j
+ * of chunk k of the upper triangle of tile pairs, tile side `tile` (tile pairs
+ * (I, J), I <= J, numbered row by row; chunk k is tile pairs
+ * [k*chunk, (k+1)*chunk)).
+ *   slots     host array of capacity `cap` doubles (may be NULL to query sizes).
+ *   info      host int64[4]: {tile, chunk, n_tile_pairs, n_slots}.
+ * Errors: KDE_ERR_INVALID when cap < n_slots and slots != NULL.
+ */
+KDE_API kde_status kde_psi_slots(const double* x, int64_t n, int r, double g, kde_precision prec,
+                         double* slots, int64_t cap, int64_t* info);
+
+/* ---- serving: continuous batching of bandwidth-selection requests ---------- */
+
+typedef struct kde_server kde_server;
+
+typedef struct {
+    size_t hbm_budget_bytes;   /* device memory the server may hold for requests */
+    int32_t max_inflight;      /* admitted requests at most (>= 1) */
+    int32_t device;            /* CUDA device ordinal */
+    double tick_target_ms;     /* device time per scheduling tick (<= 0: default) */
+} kde_server_config;
+
+/* Per-request timing, host clock, nanoseconds since server creation. */
+typedef struct {
+    int64_t n;
+    int32_t precision;
+    int32_t status;
+    int64_t t_submit_ns, t_admit_ns, t_done_ns;
+} kde_request_times;
+
+/* Create a server; it reserves its device arena and starts its host thread. */
+KDE_API kde_status kde_server_create(const kde_server_config* cfg, kde_server** out);
+/* Enqueue one request; x (host, n binary32 values) is copied before return. */
+KDE_API kde_status kde_server_submit(kde_server* s, const float* x, int64_t n, kde_precision prec,
+                             uint64_t* ticket);
+/* Wait up to timeout_ms (< 0: forever) for a ticket; KDE_ERR_TIMEOUT if not done.
+ * A finished ticket's result is returned once and then forgotten. */
+KDE_API kde_status kde_server_poll(kde_server* s, uint64_t ticket, int32_t timeout_ms,
+                           kde_result* out, kde_request_times* times);
+/* Stop accepting, finish admitted work, free everything. */
+KDE_API void kde_server_destroy(kde_server* s);
+
+/* ---- profiling ----------------------------------------------------------------- */
+
+/* Turn kernel timing on or off (process-wide, off by default).  While on, every
+ * run records CUDA events around its kernels on the caller's stream (inside the
+ * captured graph too). */
+KDE_API kde_status kde_profile_enable(int on);
+/* Wait for the last profiled run on `stream` and write the device time in ms of
+ * its kernels: ms[0] init, moments (Steps I-III) and the first prescale;
+ * ms[1] pairs r = 6 (Steps IV-V; for kde_psi the one pairs launch); ms[2] the
+ * second prescale; ms[3] pairs r = 4 (Steps VI-VII).  ms[2] and ms[3] are 0 for
+ * kde_psi.  cap >= 4.  KDE_ERR_INVALID if no profiled run happened there. */
+KDE_API kde_status kde_profile_last(void* stream, double* ms, int cap);
+
+/* Measure sustained per-SM throughputs with dedicated microbenchmark kernels on
+ * the current device (every block resident, CUDA-event timing): out[0] FP32 FMA
+ * lane-operations per second per SM, out[1] MUFU ex2 results per second per SM,
+ * out[2] FP64 FMA lane-operations per second per SM, out[3] SM count, out[4]
+ * ticks per second of the SM cycle counter during the FP32 run.  cap >= 5.
+ * Divided by the SM clock these size the ALU roofline of the pair kernels. */
+KDE_API kde_status kde_probe_pipe_rates(double* out, int cap);
+
+/* ---- misc -------------------------------------------------------------------- */
+
+/* Thread-local text of the last error on this thread ("" if none). */
+KDE_API const char* kde_last_error(void);
+/* Library version string. */
+KDE_API const char* kde_version(void);
+/* Free the library's cached device workspaces and graphs (optional). */
+KDE_API void kde_shutdown(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* KDE_H */

@@ -1,0 +1,707 @@
+// kde_kernels.cu -- device code of libkde.
+//
+// Algorithm 1 of Gramacki, Sawerwain & Gramacki runs as these kernels per batch:
+//   moments_kernel   Step I (mean, unbiased variance), Steps II-III (psi8^NS, g1)
+//   pairs_kernel<6>  Step IV (psi6(g1), Eq. 6) and Step V (g2)
+//   pairs_kernel<4>  Step VI (psi4(g2), Eq. 7) and Step VII (h)
+// The last CTA to finish a sample's share of a kernel takes that sample's next
+// scalar step, so no scalar goes back to the host between steps.
+//
+// Before them, every sample is sorted (kde_sort.cu) and, per psi, scaled once
+// (prescale_kernel): binary32 samples onto an exact-difference grid, binary64
+// samples to u-units (X - median) / g.  The pair kernels evaluate K^(r)(u) =
+// He_r(u) phi(u) for every unique pair, u = (X_i - X_j) / g: the binary32 path
+// spends an exact FADD for the difference, an FMUL for u^2, a clamp, 6
+// instructions of range reduction and exponent insertion plus an 8-FFMA
+// polynomial for exp(-u^2/2), r/2 Horner FFMAs on the integer Hermite
+// coefficients, one FMUL for the term and four instructions of compensated
+// accumulation.  The 1/sqrt(2 pi), the factor 2 and the diagonal n K^(r)(0)
+// of Eqs. 6-7 are applied once, in binary64, at the end.
+#include "kde_internal.cuh"
+
+#include <math_constants.h>
+
+#include <cfloat>
+#include <cmath>
+
+namespace kde {
+namespace {
+
+// ---------------------------------------------------------------------------
+// small helpers
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ float ex2_approx_ftz(float t) {
+  float e;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(e) : "f"(t));
+  return e;
+}
+
+__device__ __forceinline__ double load_x(const void* x, int f32, int64_t i) {
+  return f32 ? static_cast<double>(__ldg(static_cast<const float*>(x) + i))
+             : __ldg(static_cast<const double*>(x) + i);
+}
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Sum over the block in a fixed order (warp trees, then warps in index order);
+// every thread gets the result.  `red` holds THREADS/32 + 1 doubles.
+template <int THREADS>
+__device__ double block_sum(double v, double* red) {
+  v = warp_sum(v);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    for (int i = 0; i < THREADS / 32; ++i) s += red[i];
+    red[THREADS / 32] = s;
+  }
+  __syncthreads();
+  const double r = red[THREADS / 32];
+  __syncthreads();
+  return r;
+}
+
+template <int THREADS, bool MAX>
+__device__ double block_minmax(double v, double* red) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const double u = __shfl_down_sync(0xffffffffu, v, o);
+    v = MAX ? fmax(v, u) : fmin(v, u);
+  }
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s = red[0];
+    for (int i = 1; i < THREADS / 32; ++i) s = MAX ? fmax(s, red[i]) : fmin(s, red[i]);
+    red[THREADS / 32] = s;
+  }
+  __syncthreads();
+  const double r = red[THREADS / 32];
+  __syncthreads();
+  return r;
+}
+
+__device__ __forceinline__ void set_nan_result(kde_result& r) {
+  const double q = CUDART_NAN;
+  r.mean = r.sigma = r.psi8 = r.g1 = r.psi6 = r.g2 = r.psi4 = r.h = q;
+}
+
+// Representation of the next psi evaluation at bandwidth g (see the notes in
+// kde_internal.cuh): scale, binary32 grid exponent F and padding values.  Returns false (and sets KDE_ERR_INVALID) when g or the data
+// range cannot be represented.  Padding sits kPadMargin bandwidths beyond the
+// data on either side, so every term that involves it is exactly zero.
+__device__ bool set_psi_scale(SampleState* st, double g, int prec) {
+  if (!(g > 0.0) || !isfinite(g)) {
+    st->res.status = KDE_ERR_INVALID;
+    return false;
+  }
+  const double c = st->center;
+  const double W = fmax(st->xmax - c, c - st->xmin) / g;   // max |u| of any sample from c
+  st->g_cur = g;
+  if (prec == KDE_FP32) {
+    // bulk radius in u-units: the window [-2^(22-F), 2^(22-F)) holds it
+    const double bulk = fmax(st->qhi - c, c - st->qlo) / g;
+    const double zr = fmin(W, 2.0 * bulk);
+    int F = kFMax;
+    if (zr > 0.0) F = 21 - static_cast<int>(floor(log2(zr)));
+    F = F < kFMin ? kFMin : (F > kFMax ? kFMax : F);
+    const double two_f = ldexp(1.0, F);
+    if (!(W * two_f < kFp32RangeLimit)) {
+      st->res.status = KDE_ERR_INVALID;
+      return false;
+    }
+    const double P = (W + kPadMargin) * two_f;
+    st->F = F;
+    st->scale = two_f / g;
+    st->pad_lo = kYBias - P;
+    st->pad_hi = kYBias + P;
+  } else {
+    if (!(W < kFp64RangeLimit)) {
+      st->res.status = KDE_ERR_INVALID;
+      return false;
+    }
+    st->F = 0;
+    st->scale = 1.0 / g;
+    st->pad_hi = W + kPadMargin;
+    st->pad_lo = -st->pad_hi;
+  }
+  return true;
+}
+
+// ---------------------------------------------------------------------------
+// init: every result field NaN, status OK (or INVALID for n < 2), counters 0
+// ---------------------------------------------------------------------------
+
+__global__ void init_states_kernel(const SampleDesc* desc, SampleState* state, int64_t m,
+                                   unsigned long long* counters, int n_counters) {
+  const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (k < n_counters) counters[k] = 0ull;
+  if (k >= m) return;
+  SampleState* st = state + k;
+  set_nan_result(st->res);
+  st->res.status = desc[k].n >= 2 ? KDE_OK : KDE_ERR_INVALID;
+  st->res.reserved = 0;
+  st->xmin = st->xmax = st->g_cur = st->scale = st->pad_lo = st->pad_hi = st->psi_out = CUDART_NAN;
+  st->center = st->qlo = st->qhi = CUDART_NAN;
+  st->F = 0;
+  st->reserved = 0;
+  st->done_mom = 0;
+  st->done_pairs = 0;
+}
+
+// ---------------------------------------------------------------------------
+// Step I (+ Steps II-III): per-block two-pass moments, merged in block order
+// ---------------------------------------------------------------------------
+
+struct Moments {
+  double cnt, mean, m2, mn, mx;
+};
+
+// Chan, Golub & LeVeque pairwise update of (count, mean, M2).
+__device__ __forceinline__ Moments merge(const Moments& a, const Moments& b) {
+  if (b.cnt == 0.0) return a;
+  if (a.cnt == 0.0) return b;
+  Moments r;
+  r.cnt = a.cnt + b.cnt;
+  const double delta = b.mean - a.mean;
+  r.mean = a.mean + delta * (b.cnt / r.cnt);
+  r.m2 = a.m2 + b.m2 + delta * delta * (a.cnt * b.cnt / r.cnt);
+  r.mn = fmin(a.mn, b.mn);
+  r.mx = fmax(a.mx, b.mx);
+  return r;
+}
+
+__global__ void __launch_bounds__(kMomThreads) moments_kernel(MomentsArgs a) {
+  __shared__ double red[kMomThreads / 32 + 1];
+  __shared__ Moments tup[kMomMaxBlocks];
+  __shared__ int s_last;
+  const int tid = threadIdx.x;
+
+  // which sample does this block belong to (prefix sums of blocks per sample)
+  const int64_t b = blockIdx.x;
+  int64_t lo = 0, hi = a.m;
+  while (hi - lo > 1) {
+    const int64_t mid = (lo + hi) >> 1;
+    if (a.mprefix[mid] <= b) lo = mid; else hi = mid;
+  }
+  const int64_t k = a.ids ? static_cast<int64_t>(a.ids[lo]) : lo;
+  const SampleDesc d = a.desc[k];
+  SampleState* st = a.state + k;
+  const int64_t lb = b - a.mprefix[lo];
+  const int64_t i0 = lb * d.mchunk;
+  const int64_t i1 = (i0 + d.mchunk < d.n) ? i0 + d.mchunk : d.n;
+
+  // pass 1: block-local mean
+  double s = 0.0;
+  for (int64_t i = i0 + tid; i < i1; i += kMomThreads) s += load_x(a.x, a.x_is_f32, d.x_off + i);
+  const double cnt = static_cast<double>(i1 - i0);
+  const double lmean = block_sum<kMomThreads>(s, red) / cnt;
+  // pass 2: sum of squared deviations from the local mean, min, max
+  double q = 0.0, mn = CUDART_INF, mx = -CUDART_INF;
+  for (int64_t i = i0 + tid; i < i1; i += kMomThreads) {
+    const double v = load_x(a.x, a.x_is_f32, d.x_off + i);
+    const double c = v - lmean;
+    q += c * c;
+    mn = fmin(mn, v);
+    mx = fmax(mx, v);
+    if (!isfinite(v)) q = CUDART_NAN;   // propagate: non-finite data is invalid
+  }
+  q = block_sum<kMomThreads>(q, red);
+  mn = block_minmax<kMomThreads, false>(mn, red);
+  mx = block_minmax<kMomThreads, true>(mx, red);
+
+  if (tid == 0) {
+    double* t = a.mslots + d.mslot_off + lb * 5;
+    t[0] = cnt; t[1] = lmean; t[2] = q; t[3] = mn; t[4] = mx;
+    __threadfence();
+    const unsigned prev = atomicAdd(&st->done_mom, 1u);
+    s_last = (prev + 1 == static_cast<unsigned>(d.mblocks));
+  }
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+
+  // last block of this sample: merge the block tuples in a fixed tree order
+  const int nb = static_cast<int>(d.mblocks);
+  if (tid < nb) {
+    const double* t = a.mslots + d.mslot_off + tid * 5;
+    tup[tid] = Moments{__ldcg(t), __ldcg(t + 1), __ldcg(t + 2), __ldcg(t + 3), __ldcg(t + 4)};
+  }
+  __syncthreads();
+  for (int stride = 1; stride < nb; stride <<= 1) {
+    if ((tid % (2 * stride)) == 0 && tid + stride < nb) tup[tid] = merge(tup[tid], tup[tid + stride]);
+    __syncthreads();
+  }
+  if (tid != 0) return;
+
+  st->done_mom = 0;
+  const Moments M = tup[0];
+  const double n = static_cast<double>(d.n);
+  st->res.mean = M.mean;
+  st->xmin = M.mn;
+  st->xmax = M.mx;
+  if (!isfinite(M.mean) || !isfinite(M.m2) || !isfinite(M.mn) || !isfinite(M.mx)) {
+    st->res.status = KDE_ERR_INVALID;
+    return;
+  }
+  const double sigma = sqrt(M.m2 / (n - 1.0));            // Step I
+  st->res.sigma = sigma;
+  {  // the sample is sorted: median and 0.1% / 99.9% quantiles by index
+    const int64_t ilo = (d.n - 1) / 1000, ihi = d.n - 1 - ilo, imid = (d.n - 1) / 2;
+    st->center = load_x(a.x, a.x_is_f32, d.x_off + imid);
+    st->qlo = load_x(a.x, a.x_is_f32, d.x_off + ilo);
+    st->qhi = load_x(a.x, a.x_is_f32, d.x_off + ihi);
+  }
+  double g;
+  if (d.g_fixed > 0.0) {
+    g = d.g_fixed;                                          // stand-alone psi_r(g)
+  } else {
+    if (!(sigma > 0.0)) {
+      st->res.status = KDE_ERR_DEGENERATE;
+      return;
+    }
+    const double psi8 = 105.0 / (32.0 * sqrt(kPi) * pow(sigma, 9.0));   // Step II
+    const double k6_0 = -15.0 / sqrt(2.0 * kPi);                          // K^(6)(0)
+    const double g1 = pow(-2.0 * k6_0 / (psi8 * n), 1.0 / 9.0);           // Step III, mu2 = 1
+    st->res.psi8 = psi8;
+    st->res.g1 = g1;
+    g = g1;
+  }
+  set_psi_scale(st, g, d.prec);
+}
+
+// ---------------------------------------------------------------------------
+// Scaled values for the pair kernel, once per sample and psi (O(n))
+// ---------------------------------------------------------------------------
+
+__global__ void __launch_bounds__(kPrescaleThreads) prescale_kernel(PrescaleArgs a) {
+  const int64_t b = blockIdx.x;
+  int64_t lo = 0, hi = a.m;
+  while (hi - lo > 1) {
+    const int64_t mid = (lo + hi) >> 1;
+    if (a.bprefix[mid] <= b) lo = mid; else hi = mid;
+  }
+  const int64_t k = a.ids ? static_cast<int64_t>(a.ids[lo]) : lo;
+  const SampleDesc& d = a.desc[k];
+  const int64_t i = (b - a.bprefix[lo]) * kPrescaleThreads + threadIdx.x;
+  if (i >= d.n) return;
+  const SampleState& st = a.state[k];
+  if (st.res.status != KDE_OK) return;
+  const double z = __dmul_rn(__dsub_rn(load_x(a.x, a.x_is_f32, d.x_off + i), st.center), st.scale);
+  if (d.prec == KDE_FP32) static_cast<float*>(a.y)[d.y_off + i] = static_cast<float>(kYBias + rint(z));
+  else static_cast<double*>(a.y)[d.y_off + i] = z;
+}
+
+// ---------------------------------------------------------------------------
+// Steps IV / VI: persistent triangular-tile pair kernel
+// ---------------------------------------------------------------------------
+
+template <int PREC> struct Arith;
+template <> struct Arith<KDE_FP32> { using T = float; };
+template <> struct Arith<KDE_FP64> { using T = double; };
+
+// Hermite factor of K^(r) on v = u^2, u = (X_i - X_j)/g, with the integer
+// coefficients printed in Steps IV and VI (exact in binary32):
+//   He_6 = ((v - 15) v + 45) v - 15,   He_4 = (v - 6) v + 3.
+// `h` = 1/2 halves every coefficient exactly (diagonal tile pairs).  Rounding
+// these coefficients (e.g. after absorbing a base change into them) would
+// distort He_r, and the pair sum cancels so strongly (sum |terms| / |sum| grows
+// like (sigma/g)^6, ~1e4 at n = 2^20) that binary32 would lose several digits.
+template <typename T, int RORD>
+struct Coef {
+  T c3, c2, c1, c0;
+  // h = 1 or 1/2; p2 = 2^(-2F) turns v in grid units into u^2 (exact)
+  __device__ void set(double h, double p2) {
+    const double p4 = p2 * p2, p6 = p4 * p2;
+    if (RORD == 6) {
+      c3 = static_cast<T>(h * p6);
+      c2 = static_cast<T>(-15.0 * h * p4);
+      c1 = static_cast<T>(45.0 * h * p2);
+      c0 = static_cast<T>(-15.0 * h);
+    } else {
+      c3 = static_cast<T>(0);
+      c2 = static_cast<T>(h * p4);
+      c1 = static_cast<T>(-6.0 * h * p2);
+      c0 = static_cast<T>(3.0 * h);
+    }
+  }
+};
+
+// exp(-u^2/2) in binary32 on the FMA pipe, as 2^t with t = -u^2 / (2 ln 2).
+// In grid units t = -v c with c = 2^(-2F) / (2 ln 2) = c_hi + c_lo split into
+// two binary32 values.  k = round(t) by the 1.5 * 2^23 rounding trick (c_hi
+// suffices to pick k), f = t - k in [-1/2, 1/2] from two FFMAs (c_hi, then the
+// c_lo correction; both round full-width values, so both are unbiased), 2^f by
+// a degree-8 minimax polynomial (relative error 1.1e-12, fitted by Remez
+// exchange, p(0) = 1 exactly), and k goes straight into the exponent field.
+// The pair sum cancels so strongly (sum |terms| / |sum| ~ 2e4 for psi6 at
+// n = 2^20) that any bias of the exponential at the 1e-9 level shows: the MUFU
+// ex2 unit (~3e-8 rms) costs 1.6e-4 on psi6 at n = 2^20; rounding c to one
+// binary32 (a dilation of the Gaussian but not of He_r) costs ~2e-6 on psi4;
+// a natural-base reduction whose last step rounds a value on a grid coarser
+// than its result (t - k ln2_hi with t large) costs ~8e-6 on psi6.
+// u^2 is clamped to 125 * 2 ln 2 (~173): beyond it every term is below 1e-31,
+// the exponent stays normal and He_r stays finite.
+constexpr float kRoundMagic = 12582912.0f;                 // 1.5 * 2^23
+constexpr double kInvTwoLn2 = 0.72134752044448170367996234050095;
+constexpr float kMinT = 125.0f;
+
+__device__ __forceinline__ float exp2_reduced(float f) {
+  float q = 1.3344183e-06f;
+  q = __fmaf_rn(q, f, 1.5314209e-05f);
+  q = __fmaf_rn(q, f, 1.5403098e-04f);
+  q = __fmaf_rn(q, f, 1.3333434e-03f);
+  q = __fmaf_rn(q, f, 9.6181296e-03f);
+  q = __fmaf_rn(q, f, 5.5504110e-02f);
+  q = __fmaf_rn(q, f, 2.4022651e-01f);
+  q = __fmaf_rn(q, f, 6.9314718e-01f);
+  return __fmaf_rn(q, f, 1.0f);
+}
+
+// One pair term, binary32: a, b scaled values (grid units); c_hi + c_lo =
+// 2^(-2F) / (2 ln 2); vmax = kMinT / c_hi.
+template <int RORD>
+__device__ __forceinline__ float term32(float a, float b, const Coef<float, RORD>& cf, float c_hi,
+                                        float c_lo, float vmax) {
+  const float d = __fsub_rn(a, b);                        // exact (see kde_internal.cuh)
+  const float v = fminf(__fmul_rn(d, d), vmax);           // u^2 * 2^(2F)
+  const float yb = __fmaf_rn(v, -c_hi, kRoundMagic);      // low bits: k = round(t)
+  const float kf = __fsub_rn(yb, kRoundMagic);
+  const float f = __fmaf_rn(v, -c_lo, __fmaf_rn(v, -c_hi, -kf));   // t - k
+  const float e = __int_as_float(__float_as_int(exp2_reduced(f)) + (__float_as_int(yb) << 23));
+  float p;
+  if (RORD == 6) p = __fmaf_rn(__fmaf_rn(__fmaf_rn(cf.c3, v, cf.c2), v, cf.c1), v, cf.c0);
+  else p = __fmaf_rn(__fmaf_rn(cf.c2, v, cf.c1), v, cf.c0);
+  return __fmul_rn(p, e);
+}
+
+template <int RORD>
+__device__ __forceinline__ double term64(double a, double b, const Coef<double, RORD>& cf,
+                                         double acc) {
+  const double d = __dsub_rn(a, b);
+  const double v = __dmul_rn(d, d);
+  double p;
+  if (RORD == 6) p = fma(fma(fma(cf.c3, v, cf.c2), v, cf.c1), v, cf.c0);
+  else p = fma(fma(cf.c2, v, cf.c1), v, cf.c0);
+  return fma(p, exp(-0.5 * v), acc);
+}
+
+// Compensated (Kahan) accumulator, binary32.  The sum is s - c.
+struct Kahan32 {
+  float s = 0.0f, c = 0.0f;
+  __device__ __forceinline__ void add(float v) {
+    const float y = __fsub_rn(v, c);
+    const float t = __fadd_rn(s, y);
+    c = __fsub_rn(__fsub_rn(t, s), y);
+    s = t;
+  }
+  __device__ __forceinline__ double value() const {
+    return static_cast<double>(s) - static_cast<double>(c);
+  }
+};
+
+// One tile pair, FP32: this thread's ROWS rows against the TILE columns in
+// shared memory, into ROWS x CJ independent (instruction-level parallel)
+// Kahan-compensated sums, folded into the thread's running Kahan sum once per
+// tile pair.  Sorted tiles make the terms one accumulator sees nearly equal;
+// plain binary32 summation of such runs drifts systematically, which the
+// cancellation of the pair sum would amplify.
+template <int RORD, int ROWS, int CJ, int TILE>
+__device__ __forceinline__ void tile_pass(const float* __restrict__ tile, const float (&w)[ROWS],
+                                          const Coef<float, RORD>& cf, float c_hi, float c_lo,
+                                          float vmax, Kahan32& acc) {
+  static_assert(CJ % 4 == 0, "column groups are float4 loads");
+  float sum[ROWS][CJ], comp[ROWS][CJ];
+#pragma unroll
+  for (int r = 0; r < ROWS; ++r)
+#pragma unroll
+    for (int q = 0; q < CJ; ++q) sum[r][q] = comp[r][q] = 0.0f;
+#pragma unroll 1
+  for (int jj = 0; jj < TILE; jj += CJ) {
+    float b[CJ];
+#pragma unroll
+    for (int q4 = 0; q4 < CJ; q4 += 4) {
+      const float4 v4 = *reinterpret_cast<const float4*>(tile + jj + q4);
+      b[q4] = v4.x; b[q4 + 1] = v4.y; b[q4 + 2] = v4.z; b[q4 + 3] = v4.w;
+    }
+#pragma unroll
+    for (int r = 0; r < ROWS; ++r)
+#pragma unroll
+      for (int q = 0; q < CJ; ++q) {
+        const float y = __fsub_rn(term32<RORD>(w[r], b[q], cf, c_hi, c_lo, vmax), comp[r][q]);
+        const float t = __fadd_rn(sum[r][q], y);
+        comp[r][q] = __fsub_rn(__fsub_rn(t, sum[r][q]), y);
+        sum[r][q] = t;
+      }
+  }
+#pragma unroll
+  for (int r = 0; r < ROWS; ++r)
+#pragma unroll
+    for (int q = 0; q < CJ; ++q) acc.add(__fsub_rn(sum[r][q], comp[r][q]));
+}
+
+// One tile pair, FP64 (plain binary64 accumulation, accurate exp).
+template <int RORD, int ROWS, int TILE>
+__device__ __forceinline__ void tile_pass64(const double* __restrict__ tile,
+                                            const double (&w)[ROWS],
+                                            const Coef<double, RORD>& cf, double& acc) {
+  double part[ROWS];
+#pragma unroll
+  for (int r = 0; r < ROWS; ++r) part[r] = 0.0;
+#pragma unroll 2
+  for (int jj = 0; jj < TILE; jj += 2) {
+    const double2 b = *reinterpret_cast<const double2*>(tile + jj);
+#pragma unroll
+    for (int r = 0; r < ROWS; ++r) {
+      part[r] = term64<RORD>(w[r], b.x, cf, part[r]);
+      part[r] = term64<RORD>(w[r], b.y, cf, part[r]);
+    }
+  }
+  double seg = part[0];
+#pragma unroll
+  for (int r = 1; r < ROWS; ++r) seg += part[r];
+  acc += seg;
+}
+
+// Tile pair number p of the upper triangle (I <= J, row by row) -> (I, J).
+// Row I starts at S(I) = I nt - I (I - 1) / 2.
+__device__ __forceinline__ void tri_index(int64_t p, int64_t nt, int64_t& I, int64_t& J) {
+  const double b = 2.0 * static_cast<double>(nt) + 1.0;
+  const double disc = fmax(b * b - 8.0 * static_cast<double>(p), 0.0);
+  int64_t i = static_cast<int64_t>(floor((b - sqrt(disc)) * 0.5));
+  if (i > nt - 1) i = nt - 1;
+  if (i < 0) i = 0;
+  auto S = [nt](int64_t q) { return q * nt - q * (q - 1) / 2; };
+  while (i > 0 && S(i) > p) --i;
+  while (i + 1 < nt && S(i + 1) <= p) ++i;
+  I = i;
+  J = i + (p - S(i));
+}
+
+template <int PREC, int THREADS, int ROWS, int RORD>
+__device__ void finalize_pairs(const PairArgs& a, const SampleDesc& d, SampleState* st,
+                               double* red) {
+  double s = 0.0;
+  for (int64_t i = threadIdx.x; i < d.nchunks; i += THREADS) s += __ldcg(a.slots + d.slot_off + i);
+  s = block_sum<THREADS>(s, red);
+  if (threadIdx.x != 0) return;
+  st->done_pairs = 0;
+  if (st->res.status != KDE_OK) return;
+  const double n = static_cast<double>(d.n);
+  const double g = st->g_cur;
+  const double he0 = RORD == 6 ? -15.0 : 3.0;
+  // Eqs. 6-7: [2 sum_{i<j} K^(r) + n K^(r)(0)] / (n^2 g^(r+1)), K^(r) = He_r phi
+  const double psi = (2.0 * s + n * he0) / (sqrt(2.0 * kPi) * n * n * pow(g, RORD + 1.0));
+  if (!a.chain) {
+    st->psi_out = psi;
+    if (RORD == 6) st->res.psi6 = psi; else st->res.psi4 = psi;
+    return;
+  }
+  if (RORD == 6) {
+    st->res.psi6 = psi;
+    if (!(psi < 0.0)) { st->res.status = KDE_ERR_DOMAIN; return; }
+    const double k4_0 = 3.0 / sqrt(2.0 * kPi);                 // K^(4)(0)
+    const double g2 = pow(-2.0 * k4_0 / (psi * n), 1.0 / 7.0); // Step V, mu2 = 1
+    st->res.g2 = g2;
+    set_psi_scale(st, g2, PREC);
+  } else {
+    st->res.psi4 = psi;
+    if (!(psi > 0.0)) { st->res.status = KDE_ERR_DOMAIN; return; }
+    const double RK = 1.0 / (2.0 * sqrt(kPi));                 // R(K)
+    st->res.h = pow(RK / (psi * n), 1.0 / 5.0);                 // Step VII, mu2 = 1
+  }
+}
+
+template <int PREC, int THREADS, int ROWS, int CJ, int RORD>
+__global__ void __launch_bounds__(THREADS) pairs_kernel(PairArgs a) {
+  using T = typename Arith<PREC>::T;
+  constexpr int TILE = THREADS * ROWS;
+  static_assert(TILE % 8 == 0, "tile");
+  __shared__ __align__(16) T tile[TILE];
+  __shared__ double red[THREADS / 32 + 1];
+  __shared__ long long s_item;
+  __shared__ int s_last;
+  const int tid = threadIdx.x;
+
+  for (;;) {
+    if (tid == 0) s_item = static_cast<long long>(atomicAdd(a.counters, 1ull));
+    __syncthreads();
+    const long long item = s_item;
+    if (item >= a.n_items) break;
+    const uint64_t wi = a.items[item];
+    const int64_t k = static_cast<int64_t>(wi >> 32);
+    const int64_t c = static_cast<int64_t>(wi & 0xffffffffull);
+    const SampleDesc d = a.desc[k];
+    SampleState* st = a.state + k;
+
+    double part = 0.0;
+    double diag_units = 0.0;
+    if (st->res.status == KDE_OK) {
+      const T* __restrict__ y = static_cast<const T*>(a.y) + d.y_off;
+      const T pad_lo = static_cast<T>(st->pad_lo), pad_hi = static_cast<T>(st->pad_hi);
+      const double p2 = ldexp(1.0, -2 * st->F);
+      const float c_hi = static_cast<float>(kInvTwoLn2 * p2);
+      const float c_lo = static_cast<float>(kInvTwoLn2 * p2 - static_cast<double>(c_hi));
+      const float vmax = kMinT / c_hi;
+      Coef<T, RORD> full, half;
+      full.set(1.0, p2);
+      half.set(0.5, p2);
+      int64_t p = c * d.chunk;
+      const int64_t pend = (p + d.chunk < d.ntp) ? p + d.chunk : d.ntp;
+      int64_t I, J;
+      tri_index(p, d.nt, I, J);
+      T w[ROWS];
+      // row slot r of this thread holds sample I*TILE + tid*ROWS + r
+      auto load_rows = [&](int64_t I_) {
+#pragma unroll
+        for (int r = 0; r < ROWS; ++r) {
+          const int64_t i = I_ * TILE + static_cast<int64_t>(tid) * ROWS + r;
+          w[r] = i < d.n ? y[i] : pad_lo;
+        }
+      };
+      load_rows(I);
+      Kahan32 acc32;
+      double acc64 = 0.0;
+      for (; p < pend; ++p) {
+        __syncthreads();
+#pragma unroll
+        for (int r = 0; r < ROWS; ++r) {
+          const int64_t j = J * TILE + tid + r * THREADS;
+          tile[tid + r * THREADS] = j < d.n ? y[j] : pad_hi;
+        }
+        __syncthreads();
+        // A diagonal tile pair (I == J) is evaluated in full with halved
+        // coefficients: the i < j and j < i terms are bitwise equal, and the
+        // i == j terms are He_r(0) / 2 (to the ex2 rounding), removed below.
+        const bool diag = (I == J);
+        const Coef<T, RORD>& cf = diag ? half : full;
+        if constexpr (PREC == KDE_FP32) {
+          tile_pass<RORD, ROWS, CJ, TILE>(tile, w, cf, c_hi, c_lo, vmax, acc32);
+        } else {
+          tile_pass64<RORD, ROWS, TILE>(tile, w, cf, acc64);
+        }
+        if (diag) {
+          const int64_t valid = d.n - I * TILE;
+          diag_units += static_cast<double>(valid < TILE ? valid : TILE);
+        }
+        if (++J == d.nt) {
+          ++I;
+          J = I;
+          if (p + 1 < pend) load_rows(I);
+        }
+      }
+      part = (PREC == KDE_FP32) ? acc32.value() : acc64;
+    }
+    const double tot = block_sum<THREADS>(part, red);
+    if (tid == 0) {
+      const double he0 = RORD == 6 ? -15.0 : 3.0;
+      a.slots[d.slot_off + c] = tot - 0.5 * he0 * diag_units;
+      __threadfence();
+      const unsigned prev = atomicAdd(&st->done_pairs, 1u);
+      s_last = (prev + 1 == static_cast<unsigned>(d.nchunks));
+    }
+    __syncthreads();
+    if (s_last) {
+      __threadfence();
+      finalize_pairs<PREC, THREADS, ROWS, RORD>(a, d, st, red);
+    }
+    __syncthreads();
+  }
+  if (tid == 0) {
+    const unsigned long long e = atomicAdd(a.counters + 1, 1ull);
+    if (e + 1 == gridDim.x) {
+      a.counters[0] = 0ull;
+      a.counters[1] = 0ull;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// configuration table
+// ---------------------------------------------------------------------------
+
+using PairKernel = void (*)(PairArgs);
+
+struct ConfigEntry {
+  PairConfig cfg;
+  PairKernel k4, k6;
+};
+
+#define KDE_CFG(P, TH, RW, CJ) \
+  { {TH, RW}, pairs_kernel<P, TH, RW, CJ, 4>, pairs_kernel<P, TH, RW, CJ, 6> }
+
+const ConfigEntry kFp32Configs[] = {
+    KDE_CFG(KDE_FP32, 128, 4, 4),   // T = 512
+    KDE_CFG(KDE_FP32, 64, 8, 4),    // T = 512
+    KDE_CFG(KDE_FP32, 256, 4, 4),   // T = 1024
+    KDE_CFG(KDE_FP32, 64, 4, 4),    // T = 256
+    KDE_CFG(KDE_FP32, 128, 2, 4),   // T = 256
+};
+const ConfigEntry kFp64Configs[] = {
+    KDE_CFG(KDE_FP64, 128, 2, 4),   // T = 256
+    KDE_CFG(KDE_FP64, 128, 4, 4),   // T = 512
+    KDE_CFG(KDE_FP64, 64, 4, 4),    // T = 256
+};
+#undef KDE_CFG
+
+const ConfigEntry& entry(int prec, int cfg) {
+  return prec == KDE_FP32 ? kFp32Configs[cfg] : kFp64Configs[cfg];
+}
+
+}  // namespace
+
+int pair_config_count(int prec) {
+  return prec == KDE_FP32 ? static_cast<int>(sizeof(kFp32Configs) / sizeof(kFp32Configs[0]))
+                          : static_cast<int>(sizeof(kFp64Configs) / sizeof(kFp64Configs[0]));
+}
+
+PairConfig pair_config(int prec, int cfg) { return entry(prec, cfg).cfg; }
+
+int pair_blocks_per_sm(int prec, int cfg) {
+  static int cache[2][8] = {};
+  int& v = cache[prec == KDE_FP32 ? 0 : 1][cfg];
+  if (v == 0) {
+    const ConfigEntry& e = entry(prec, cfg);
+    int b4 = 0, b6 = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b4, e.k4, e.cfg.threads, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b6, e.k6, e.cfg.threads, 0);
+    v = b4 < b6 ? b4 : b6;
+    if (v < 1) v = 1;
+  }
+  return v;
+}
+
+cudaError_t launch_init(const SampleDesc* desc, SampleState* state, int64_t m,
+                        unsigned long long* counters, int n_counters, cudaStream_t s) {
+  const int64_t work = m > n_counters ? m : n_counters;
+  const int blocks = static_cast<int>((work + 255) / 256);
+  init_states_kernel<<<blocks, 256, 0, s>>>(desc, state, m, counters, n_counters);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_moments(const MomentsArgs& a, int64_t total_blocks, cudaStream_t s) {
+  if (total_blocks <= 0) return cudaSuccess;
+  moments_kernel<<<static_cast<unsigned>(total_blocks), kMomThreads, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_prescale(const PrescaleArgs& a, int64_t total_blocks, cudaStream_t s) {
+  if (total_blocks <= 0) return cudaSuccess;
+  prescale_kernel<<<static_cast<unsigned>(total_blocks), kPrescaleThreads, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pairs(int prec, int cfg, const PairArgs& a, int grid, cudaStream_t s) {
+  if (a.n_items <= 0 || grid <= 0) return cudaSuccess;
+  const ConfigEntry& e = entry(prec, cfg);
+  PairKernel k = a.r == 6 ? e.k6 : e.k4;
+  k<<<grid, e.cfg.threads, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+}  // namespace kde

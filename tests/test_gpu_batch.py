@@ -1,0 +1,81 @@
+"""Batched PLUGIN: many samples of uneven n in one persistent launch per step."""
+import numpy as np
+import pytest
+
+import oracle
+import synthdata
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def kde():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1505_02100_gb300 as k
+    return k
+
+
+def _pack(samples):
+    offsets = np.zeros(len(samples) + 1, dtype=np.int64)
+    offsets[1:] = np.cumsum([s.size for s in samples])
+    return np.concatenate(samples), offsets
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_batch_equals_alone_bitwise_and_oracle(kde, prec):
+    specs = synthdata.mixed_specs(24, 606, 256, 20000)
+    samples = [synthdata.sample_from_spec(s) for s in specs]
+    samples.insert(5, np.array([1.5]))            # n = 1: INVALID for that sample only
+    samples.insert(9, np.full(300, -2.0))         # sigma = 0: DEGENERATE
+    x, off = _pack(samples)
+    got = kde.kde_plugin_h_batch(x, off, prec)
+    assert got[5]["status"] == kde.KDE_ERR_INVALID
+    assert got[9]["status"] == kde.KDE_ERR_DEGENERATE
+    tol = 1e-5 if prec == 0 else 1e-11
+    for k, s in enumerate(samples):
+        if k in (5, 9):
+            continue
+        alone = kde.kde_plugin_h(s, prec)
+        assert got[k] == alone, k                      # bitwise: tiling depends only on n
+        if s.size <= 6000:
+            ref = oracle.plugin(s)
+            for f in ("psi6", "psi4", "h"):
+                assert abs(got[k][f] - ref[f]) <= tol * abs(ref[f]), (k, f)
+
+
+def test_batch_device_resident_and_replay(kde):
+    import torch
+    specs = synthdata.mixed_specs(40, 707, 256, 60000)
+    samples = [synthdata.sample_from_spec(s) for s in specs]
+    x, off = _pack(samples)
+    xd = torch.tensor(x, device="cuda")
+    out = torch.empty(len(samples) * kde.RESULT_BYTES // 8, dtype=torch.float64, device="cuda")
+    first = kde.kde_plugin_h_batch(xd, off, 0)
+    for _ in range(3):                      # graph replays
+        kde.kde_plugin_h_batch(xd, off, 0, out=out)
+    torch.cuda.synchronize()
+    vals = out.view(len(samples), -1).cpu().numpy()
+    for k in range(len(samples)):
+        assert vals[k, 7] == first[k]["h"]
+        assert first[k]["status"] == 0
+
+
+def test_full_batch_workload_statuses_and_spot_checks(kde):
+    """The 512-sample workload (n log-uniform in [256, 262144]): all succeed; the
+    smallest samples match the oracle and a few match their stand-alone runs."""
+    specs = synthdata.batch_specs()
+    samples = [synthdata.sample_from_spec(s) for s in specs]
+    x, off = _pack(samples)
+    got = kde.kde_plugin_h_batch(x, off, 0)
+    assert all(r["status"] == 0 for r in got)
+    order = np.argsort([s.size for s in samples])
+    for k in order[:6]:
+        ref = oracle.plugin(samples[k])
+        for f in ("psi6", "psi4", "h"):
+            assert abs(got[k][f] - ref[f]) <= 1e-5 * abs(ref[f]), (k, f)
+    for k in list(order[-2:]) + [int(order[len(order) // 2])]:
+        assert got[k] == kde.kde_plugin_h(samples[k], 0)
