@@ -24,6 +24,7 @@ import argparse
 import json
 import math
 import os
+import re
 import statistics
 import subprocess
 import sys
@@ -144,12 +145,32 @@ class ClockSampler:
 # FP32/INT pipes, no MUFU):
 #   FADD  d = y_i - y_j (exact on the per-sample grid)
 #   FMUL  v = d^2 ;  FMNMX  clamp of v
-#   FFMA + FADD + 2 FFMA   k = round(t), f = t - k for t = -u^2/(2 ln 2)
+#   FFMA + FADD + FFMA   k = round(t), f = t - k for t = -v c_hi
 #   8 FFMA   degree-8 polynomial for 2^f
 #   SHL + IADD   2^k into the exponent field
 #   r/2 FFMA   Horner for He_r on v (3 for He_6, 2 for He_4)
 #   FMUL   term ;  4 FADD   Kahan-compensated accumulation
-ISSUE_PER_PAIR = {6: 25, 4: 24}
+#   FMUL + FFMA   the c_lo part of the exponent, accumulated apart
+ISSUE_PER_PAIR = {6: 26, 4: 25}
+KERNEL_SOURCE = os.path.join(os.path.dirname(os.path.abspath(__file__)),
+                             "paper_1505_02100_gb300", "csrc", "kde_kernels.cu")
+TRAFFIC_FILE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "profiles",
+                            "pairs_kernel_r6_bimodal_n65536.md")
+
+
+def measured_traffic():
+    """DRAM bytes per launch of the r = 6 pair kernel from the committed ncu summary,
+    or None when the kernel source changed since those counters were taken."""
+    import hashlib
+    try:
+        text = open(TRAFFIC_FILE).read()
+    except OSError:
+        return None
+    fields = dict(re.findall(r"^- (kernel_source_sha256|dram_bytes_per_launch): `([^`]+)`", text, re.M))
+    digest = hashlib.sha256(open(KERNEL_SOURCE, "rb").read()).hexdigest()
+    if fields.get("kernel_source_sha256") != digest or "dram_bytes_per_launch" not in fields:
+        return None
+    return float(fields["dram_bytes_per_launch"])
 
 
 def alu_peak(r: int, sms: int, f_mhz: float):
@@ -218,7 +239,7 @@ def run_ours(args, ws, rank, local):
         for _ in range(warmup):
             kde.kde_plugin_h(xd, prec, out=out, stream=stream)
         stream.synchronize()
-        step_ms, k6, k4 = [], [], []
+        step_ms, k6, k4, nl = [], [], [], []
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
               for _ in range(steps)]
         barrier(ws)
@@ -233,15 +254,16 @@ def run_ours(args, ws, rank, local):
                 t = kde.kde_profile_last(stream)
                 k6.append(t["pairs6"])
                 k4.append(t["pairs4"])
+                nl.append(t["launches"])
         torch.cuda.synchronize()
         barrier(ws)
         step_ms = [a.elapsed_time(b) for a, b in ev]
         kde.kde_profile_enable(False)
-        return step_ms, k6, k4
+        return step_ms, k6, k4, nl
 
     # FP32 pair path: the headline
     with ClockSampler(local) as clk:
-        step_ms, k6, k4 = timed(kde.KDE_FP32, args.steps, args.warmup, True)
+        step_ms, k6, k4, launches = timed(kde.KDE_FP32, args.steps, args.warmup, True)
     clocks = clk.summary()
     total_s = dist_max(sum(step_ms) / 1e3, ws)
     res32 = kde.kde_plugin_h(xd, kde.KDE_FP32)
@@ -267,7 +289,7 @@ def run_ours(args, ws, rank, local):
     fp64 = None
     if not args.no_fp64:
         k = max(2, args.steps // 4)
-        ms64, k6_64, k4_64 = timed(kde.KDE_FP64, k, 1, True)
+        ms64, k6_64, k4_64, _ = timed(kde.KDE_FP64, k, 1, True)
         res64 = kde.kde_plugin_h(xd, kde.KDE_FP64)
         t64 = dist_max(sum(ms64) / 1e3, ws)
         fp64 = {"value": ws * k * pairs_per_step(n) / t64, "unit": UNIT,
@@ -299,12 +321,12 @@ def run_ours(args, ws, rank, local):
                    "precision": "fp32 pair terms, fp64 moments/reductions/scalars",
                    "l2": "flushed between steps (512 MiB write outside the timed events)",
                    "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU"},
-        "gpu_launches": 4 * args.steps,
+        "gpu_launches": int(sum(launches)),
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 8 * n,
                 "d2h_bytes_per_step": kde.RESULT_BYTES},
         "roofline": {"bound": "alu", "kernel": "pairs_kernel r=6 (Step IV)",
                      "achieved": achieved / 1e9, "peak": peak["pairs_per_s"] / 1e9, "unit": "Gpair/s",
-                     "frac": achieved / peak["pairs_per_s"], "traffic": None,
+                     "frac": achieved / peak["pairs_per_s"], "traffic": measured_traffic(),
                      "peak_basis": f"{sms} SMs x 2070 MHz x 128 issue slots / {ISSUE_PER_PAIR[6]} "
                                    f"instructions per pair = {peak['pairs_per_clk_sm']:.2f} pairs/clk/SM",
                      "pairs4_kernel": {"ms": statistics.mean(k4),
@@ -312,6 +334,10 @@ def run_ours(args, ws, rank, local):
                                        "peak": peak4["pairs_per_s"] / 1e9,
                                        "frac": pairs / (statistics.mean(k4) / 1e3) / peak4["pairs_per_s"]},
                      "pairs6_ms": k6_ms,
+                     # bound of a 7-slot MUFU-ex2 term (FADD, FMUL, 3 FFMA, ex2, FFMA), which
+                     # is cheaper but too inaccurate for the 1e-5 bar at n >= 2^20
+                     "frac_vs_mufu_sequence": achieved / (sms * 2070e6 * min(128.0 / 7.0,
+                                                                             rates_clk["mufu_ex2_per_clk_sm"])),
                      "frac_at_measured_clock": achieved / (peak["pairs_per_s"] * (clocks["sm_mhz"] or 2070.0) / 2070.0),
                      "probe": rates_clk},
         "clocks": clocks,

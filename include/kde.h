@@ -186,10 +186,12 @@ KDE_API void kde_server_destroy(kde_server* s);
  * captured graph too). */
 KDE_API kde_status kde_profile_enable(int on);
 /* Wait for the last profiled run on `stream` and write the device time in ms of
- * its kernels: ms[0] init, moments (Steps I-III) and the first prescale;
+ * its kernels: ms[0] init, sort, moments (Steps I-III) and the first prescale;
  * ms[1] pairs r = 6 (Steps IV-V; for kde_psi the one pairs launch); ms[2] the
  * second prescale; ms[3] pairs r = 4 (Steps VI-VII).  ms[2] and ms[3] are 0 for
- * kde_psi.  cap >= 4.  KDE_ERR_INVALID if no profiled run happened there. */
+ * kde_psi.  If cap >= 5, ms[4] is the number of kernel launches of that run
+ * (the kernel nodes its CUDA graph replays).  cap >= 4.  KDE_ERR_INVALID if no
+ * profiled run happened there. */
 KDE_API kde_status kde_profile_last(void* stream, double* ms, int cap);
 
 /* Measure sustained per-SM throughputs with dedicated microbenchmark kernels on

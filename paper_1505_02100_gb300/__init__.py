@@ -142,11 +142,14 @@ def kde_profile_enable(on: bool = True) -> None:
 
 
 def kde_profile_last(stream=None):
-    """Device ms of the last profiled run on `stream`: setup (init + moments +
-    prescale), pairs6, prescale4, pairs4."""
-    ms = (ctypes.c_double * 4)()
-    _check(load().kde_profile_last(_stream(stream), ctypes.addressof(ms), 4))
-    return dict(zip(("setup", "pairs6", "prescale4", "pairs4"), list(ms)))
+    """Device ms of the last profiled run on `stream`: setup (init + sort +
+    moments + prescale), pairs6, prescale4, pairs4; and `launches`, the number
+    of kernel launches of that run."""
+    ms = (ctypes.c_double * 5)()
+    _check(load().kde_profile_last(_stream(stream), ctypes.addressof(ms), 5))
+    out = dict(zip(("setup", "pairs6", "prescale4", "pairs4"), list(ms)[:4]))
+    out["launches"] = int(ms[4])
+    return out
 
 
 def kde_probe_pipe_rates():

@@ -220,12 +220,17 @@ struct Workspace {
   std::mutex mu;
   DevBuf x, y, desc, state, mprefix, bprefix, sprefix, scounts, mslots, slots, items, counters;
   uint64_t meta_key = 0;
-  std::unordered_map<uint64_t, cudaGraphExec_t> graphs;
+  struct GraphEntry {
+    cudaGraphExec_t exec;
+    int launches;   // kernel launches it replays
+  };
+  std::unordered_map<uint64_t, GraphEntry> graphs;
+  int last_launches = 0;   // kernel launches of the last run on this workspace
   cudaEvent_t prof[5] = {};   // before init, after prescale r=6, after pairs r=6, after prescale r=4, after pairs r=4
   bool prof_valid = false;
 
   void drop_graphs() {
-    for (auto& kv : graphs) cudaGraphExecDestroy(kv.second);
+    for (auto& kv : graphs) cudaGraphExecDestroy(kv.second.exec);
     graphs.clear();
   }
   void release() {
@@ -334,8 +339,10 @@ kde_status enqueue(Workspace& W, const BatchPlan& P, cudaStream_t s) {
   auto* state = static_cast<SampleState*>(W.state.p);
   auto* counters = static_cast<unsigned long long*>(W.counters.p);
   const bool prof = g_profile.load() != 0;
+  int launches = 0;
   if (prof) KDE_CU(prof_record(W.prof[0], s));
   KDE_CU(launch_init(desc, state, m, counters, n_counters, s));
+  launches += m > 0 ? 1 : 0;
   SortArgs sa{};
   sa.x_is_f32 = P.x_f32;
   sa.desc = desc;
@@ -344,6 +351,7 @@ kde_status enqueue(Workspace& W, const BatchPlan& P, cudaStream_t s) {
   sa.m = m;
   sa.counts = static_cast<uint32_t*>(W.scounts.p);
   KDE_CU(launch_sort(sa, P.sprefix[m], W.x.p, W.y.p, s));
+  if (P.sprefix[m] > 0 && m > 0) launches += 3 * (P.x_f32 ? 4 : 8);   // histogram, scan, scatter per pass
   MomentsArgs ma{};
   ma.x = W.x.p;
   ma.x_is_f32 = P.x_f32;
@@ -354,6 +362,7 @@ kde_status enqueue(Workspace& W, const BatchPlan& P, cudaStream_t s) {
   ma.m = m;
   ma.mslots = static_cast<double*>(W.mslots.p);
   KDE_CU(launch_moments(ma, P.mprefix[m], s));
+  launches += P.mprefix[m] > 0 ? 1 : 0;
   PrescaleArgs pr{};
   pr.x = W.x.p;
   pr.x_is_f32 = P.x_f32;
@@ -370,6 +379,7 @@ kde_status enqueue(Workspace& W, const BatchPlan& P, cudaStream_t s) {
   for (size_t o = 0; o < orders.size(); ++o) {
     const int r = orders[o];
     KDE_CU(launch_prescale(pr, P.bprefix[m], s));
+    launches += P.bprefix[m] > 0 ? 1 : 0;
     if (prof) KDE_CU(prof_record(W.prof[o == 0 ? 1 : 3], s));
     for (const Group& g : P.groups) {
       PairArgs pa{};
@@ -383,6 +393,7 @@ kde_status enqueue(Workspace& W, const BatchPlan& P, cudaStream_t s) {
       pa.r = r;
       pa.chain = P.mode == kPlugin ? 1 : 0;
       KDE_CU(launch_pairs(P.prec, g.cfg, pa, g.grid, s));
+      launches += g.grid > 0 ? 1 : 0;
       ++L;
     }
     if (prof) KDE_CU(prof_record(W.prof[o == 0 ? 2 : 4], s));
@@ -392,6 +403,7 @@ kde_status enqueue(Workspace& W, const BatchPlan& P, cudaStream_t s) {
     KDE_CU(prof_record(W.prof[4], s));
   }
   W.prof_valid = prof;
+  W.last_launches = launches;
   return KDE_OK;
 }
 
@@ -439,9 +451,10 @@ kde_status run_plan(Workspace& W, const BatchPlan& P, const void* x, bool x_dev,
     ce = cudaGraphInstantiate(&exec, graph, 0);
     cudaGraphDestroy(graph);
     if (ce != cudaSuccess) return set_err(KDE_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(ce));
-    it = W.graphs.emplace(gkey, exec).first;
+    it = W.graphs.emplace(gkey, Workspace::GraphEntry{exec, W.last_launches}).first;
   }
-  KDE_CU(cudaGraphLaunch(it->second, s));
+  KDE_CU(cudaGraphLaunch(it->second.exec, s));
+  W.last_launches = it->second.launches;
   return KDE_OK;
 }
 
@@ -578,6 +591,7 @@ kde_status kde_profile_enable(int on) {
 
 kde_status kde_profile_last(void* stream, double* ms, int cap) {
   if (!ms || cap < 4) return set_err(KDE_ERR_INVALID, "need room for 4 durations");
+  if (cap >= 5) ms[4] = 0.0;
   Workspace* W = nullptr;
   kde_status st = get_workspace(static_cast<cudaStream_t>(stream), &W);
   if (st != KDE_OK) return st;
@@ -589,6 +603,7 @@ kde_status kde_profile_last(void* stream, double* ms, int cap) {
     KDE_CU(cudaEventElapsedTime(&v, W->prof[i], W->prof[i + 1]));
     ms[i] = v;
   }
+  if (cap >= 5) ms[4] = W->last_launches;
   return KDE_OK;
 }
 

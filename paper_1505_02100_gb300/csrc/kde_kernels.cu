@@ -334,17 +334,30 @@ struct Coef {
 
 // exp(-u^2/2) in binary32 on the FMA pipe, as 2^t with t = -u^2 / (2 ln 2).
 // In grid units t = -v c with c = 2^(-2F) / (2 ln 2) = c_hi + c_lo split into
-// two binary32 values.  k = round(t) by the 1.5 * 2^23 rounding trick (c_hi
-// suffices to pick k), f = t - k in [-1/2, 1/2] from two FFMAs (c_hi, then the
-// c_lo correction; both round full-width values, so both are unbiased), 2^f by
-// a degree-8 minimax polynomial (relative error 1.1e-12, fitted by Remez
-// exchange, p(0) = 1 exactly), and k goes straight into the exponent field.
+// two binary32 values.  k = round(v c_hi) by the 1.5 * 2^23 rounding trick,
+// f = k - v c_hi in [-1/2, 1/2] from one FFMA (the exact value of a 48-bit
+// product minus an integer, rounded once), 2^f by a degree-8 minimax
+// polynomial (relative error 1.1e-12, fitted by Remez exchange, p(0) = 1
+// exactly), and k goes straight into the exponent field.  That is
+// exp(-u^2/2) scaled by 2^(-v c_lo) = 1 - v c_lo ln 2 + O(1e-12).
+//
+// The c_lo factor is not applied to f or to the term: there it would be a
+// smooth correction a few units in the last place, added to a value already
+// on the binary32 grid, and rounding would drop the same fraction of it from
+// every term -- a bias.  Instead the caller accumulates -term * (v c_lo ln 2)
+// in a separate binary32 sum per row (`corr`, one FFMA per pair), and adds
+// those sums to a binary64 total of its own.  (Folding them into the Kahan
+// sum does not work: its compensation term keeps only the bits above half an
+// ulp of the next, much larger, partial sum added to it.)
+//
 // The pair sum cancels so strongly (sum |terms| / |sum| ~ 2e4 for psi6 at
-// n = 2^20) that any bias of the exponential at the 1e-9 level shows: the MUFU
-// ex2 unit (~3e-8 rms) costs 1.6e-4 on psi6 at n = 2^20; rounding c to one
-// binary32 (a dilation of the Gaussian but not of He_r) costs ~2e-6 on psi4;
-// a natural-base reduction whose last step rounds a value on a grid coarser
-// than its result (t - k ln2_hi with t large) costs ~8e-6 on psi6.
+// n = 2^20, growing like (sigma/g)^6) that any bias of the exponential at the
+// 1e-10 level shows.  Measured or projected exactly over every grid distance
+// on normal data at n = 2^20: the MUFU ex2 unit (~3e-8 rms) costs 1.6e-4 on
+// psi6; rounding c to one binary32 (a dilation of the Gaussian but not of
+// He_r) ~2e-6 on psi4; folding c_lo into f ~1e-5 on psi6; a natural-base
+// reduction whose last step rounds a value on a grid coarser than its result
+// (t - k ln2_hi with t large) ~8e-6 on psi6.
 // u^2 is clamped to 125 * 2 ln 2 (~173): beyond it every term is below 1e-31,
 // the exponent stays normal and He_r stays finite.
 constexpr float kRoundMagic = 12582912.0f;                 // 1.5 * 2^23
@@ -363,20 +376,22 @@ __device__ __forceinline__ float exp2_reduced(float f) {
   return __fmaf_rn(q, f, 1.0f);
 }
 
-// One pair term, binary32: a, b scaled values (grid units); c_hi + c_lo =
-// 2^(-2F) / (2 ln 2); vmax = kMinT / c_hi.
+// One pair term, binary32, without its 2^(-v c_lo) factor: a, b scaled values
+// (grid units); c_hi = 2^(-2F) / (2 ln 2) rounded; vmax = kMinT / c_hi.
+// `dl` receives v c_lo ln 2, the relative amount by which the term is too large.
 template <int RORD>
 __device__ __forceinline__ float term32(float a, float b, const Coef<float, RORD>& cf, float c_hi,
-                                        float c_lo, float vmax) {
+                                        float c_lo_ln2, float vmax, float& dl) {
   const float d = __fsub_rn(a, b);                        // exact (see kde_internal.cuh)
   const float v = fminf(__fmul_rn(d, d), vmax);           // u^2 * 2^(2F)
   const float yb = __fmaf_rn(v, -c_hi, kRoundMagic);      // low bits: k = round(t)
   const float kf = __fsub_rn(yb, kRoundMagic);
-  const float f = __fmaf_rn(v, -c_lo, __fmaf_rn(v, -c_hi, -kf));   // t - k
+  const float f = __fmaf_rn(v, -c_hi, -kf);               // t - k (c_hi part)
   const float e = __int_as_float(__float_as_int(exp2_reduced(f)) + (__float_as_int(yb) << 23));
   float p;
   if (RORD == 6) p = __fmaf_rn(__fmaf_rn(__fmaf_rn(cf.c3, v, cf.c2), v, cf.c1), v, cf.c0);
   else p = __fmaf_rn(__fmaf_rn(cf.c2, v, cf.c1), v, cf.c0);
+  dl = __fmul_rn(v, c_lo_ln2);
   return __fmul_rn(p, e);
 }
 
@@ -408,19 +423,23 @@ struct Kahan32 {
 // One tile pair, FP32: this thread's ROWS rows against the TILE columns in
 // shared memory, into ROWS x CJ independent (instruction-level parallel)
 // Kahan-compensated sums, folded into the thread's running Kahan sum once per
-// tile pair.  Sorted tiles make the terms one accumulator sees nearly equal;
-// plain binary32 summation of such runs drifts systematically, which the
-// cancellation of the pair sum would amplify.
+// tile pair, plus one c_lo correction sum per row (see term32), added to the
+// thread's binary64 correction total `cacc`.  Sorted tiles
+// make the terms one accumulator sees nearly equal; plain binary32 summation
+// of such runs drifts systematically, which the cancellation of the pair sum
+// would amplify.
 template <int RORD, int ROWS, int CJ, int TILE>
 __device__ __forceinline__ void tile_pass(const float* __restrict__ tile, const float (&w)[ROWS],
-                                          const Coef<float, RORD>& cf, float c_hi, float c_lo,
-                                          float vmax, Kahan32& acc) {
+                                          const Coef<float, RORD>& cf, float c_hi, float c_lo_ln2,
+                                          float vmax, Kahan32& acc, double& cacc) {
   static_assert(CJ % 4 == 0, "column groups are float4 loads");
-  float sum[ROWS][CJ], comp[ROWS][CJ];
+  float sum[ROWS][CJ], comp[ROWS][CJ], corr[ROWS];
 #pragma unroll
-  for (int r = 0; r < ROWS; ++r)
+  for (int r = 0; r < ROWS; ++r) {
+    corr[r] = 0.0f;
 #pragma unroll
     for (int q = 0; q < CJ; ++q) sum[r][q] = comp[r][q] = 0.0f;
+  }
 #pragma unroll 1
   for (int jj = 0; jj < TILE; jj += CJ) {
     float b[CJ];
@@ -433,16 +452,21 @@ __device__ __forceinline__ void tile_pass(const float* __restrict__ tile, const 
     for (int r = 0; r < ROWS; ++r)
 #pragma unroll
       for (int q = 0; q < CJ; ++q) {
-        const float y = __fsub_rn(term32<RORD>(w[r], b[q], cf, c_hi, c_lo, vmax), comp[r][q]);
+        float dl;
+        const float term = term32<RORD>(w[r], b[q], cf, c_hi, c_lo_ln2, vmax, dl);
+        corr[r] = __fmaf_rn(term, -dl, corr[r]);
+        const float y = __fsub_rn(term, comp[r][q]);
         const float t = __fadd_rn(sum[r][q], y);
         comp[r][q] = __fsub_rn(__fsub_rn(t, sum[r][q]), y);
         sum[r][q] = t;
       }
   }
 #pragma unroll
-  for (int r = 0; r < ROWS; ++r)
+  for (int r = 0; r < ROWS; ++r) {
 #pragma unroll
     for (int q = 0; q < CJ; ++q) acc.add(__fsub_rn(sum[r][q], comp[r][q]));
+    cacc += static_cast<double>(corr[r]);
+  }
 }
 
 // One tile pair, FP64 (plain binary64 accumulation, accurate exp).
@@ -546,7 +570,8 @@ __global__ void __launch_bounds__(THREADS) pairs_kernel(PairArgs a) {
       const T pad_lo = static_cast<T>(st->pad_lo), pad_hi = static_cast<T>(st->pad_hi);
       const double p2 = ldexp(1.0, -2 * st->F);
       const float c_hi = static_cast<float>(kInvTwoLn2 * p2);
-      const float c_lo = static_cast<float>(kInvTwoLn2 * p2 - static_cast<double>(c_hi));
+      const float c_lo_ln2 =
+          static_cast<float>((kInvTwoLn2 * p2 - static_cast<double>(c_hi)) * 0.69314718055994530942);
       const float vmax = kMinT / c_hi;
       Coef<T, RORD> full, half;
       full.set(1.0, p2);
@@ -566,6 +591,7 @@ __global__ void __launch_bounds__(THREADS) pairs_kernel(PairArgs a) {
       };
       load_rows(I);
       Kahan32 acc32;
+      double cacc = 0.0;
       double acc64 = 0.0;
       for (; p < pend; ++p) {
         __syncthreads();
@@ -581,7 +607,7 @@ __global__ void __launch_bounds__(THREADS) pairs_kernel(PairArgs a) {
         const bool diag = (I == J);
         const Coef<T, RORD>& cf = diag ? half : full;
         if constexpr (PREC == KDE_FP32) {
-          tile_pass<RORD, ROWS, CJ, TILE>(tile, w, cf, c_hi, c_lo, vmax, acc32);
+          tile_pass<RORD, ROWS, CJ, TILE>(tile, w, cf, c_hi, c_lo_ln2, vmax, acc32, cacc);
         } else {
           tile_pass64<RORD, ROWS, TILE>(tile, w, cf, acc64);
         }
@@ -595,7 +621,7 @@ __global__ void __launch_bounds__(THREADS) pairs_kernel(PairArgs a) {
           if (p + 1 < pend) load_rows(I);
         }
       }
-      part = (PREC == KDE_FP32) ? acc32.value() : acc64;
+      part = (PREC == KDE_FP32) ? acc32.value() + cacc : acc64;
     }
     const double tot = block_sum<THREADS>(part, red);
     if (tid == 0) {
