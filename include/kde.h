@@ -148,6 +148,33 @@ KDE_API kde_status kde_plugin_h_batch(const double* x_packed, const int64_t* off
 KDE_API kde_status kde_psi_slots(const double* x, int64_t n, int r, double g, kde_precision prec,
                          double* slots, int64_t cap, int64_t* info);
 
+/* ---- allocation-free variant ---------------------------------------------------- */
+
+/* Largest n kde_psi_static accepts. */
+#define KDE_STATIC_MAX_N 65536
+
+/*
+ * kde_psi_static -- psi_r(g) exactly as kde_psi computes it (Steps IV / VI,
+ * Eqs. 6-7), for n <= KDE_STATIC_MAX_N, using only a fixed scratch area of
+ * about 1.6 MB compiled into the library as a device variable.  The paper has
+ * no counterpart: this exists for callers that must not allocate device memory
+ * on the call path, e.g. a process whose framework allocator already holds
+ * most of HBM, or a latency-bound loop where cudaMalloc / cudaFree would
+ * synchronise the device.  The call itself performs no device allocation.
+ *   x       n binary64 values, host or device pointer (read only).
+ *   out     1 double, host or device.  Host: the call waits for the result.
+ *           Device: asynchronous on `stream`.
+ * Set-up: the first call on a device, with that device current, looks up the
+ * scratch area's address once (cudaGetSymbolAddress) and caches it; make that
+ * first call before any stream capture meant to contain later calls.
+ * Concurrency: one scratch area per device; calls that overlap on the device
+ * (other streams or host threads) race on it -- order them on one stream.
+ * Errors: KDE_ERR_INVALID for n > KDE_STATIC_MAX_N (message says so), n < 2,
+ * r not in {4, 6}, g <= 0 or not finite, null pointers, a bad precision.
+ */
+KDE_API kde_status kde_psi_static(const double* x, int64_t n, int r, double g, kde_precision prec,
+                                  double* out, void* stream);
+
 /* ---- serving: continuous batching of bandwidth-selection requests ---------- */
 
 typedef struct kde_server kde_server;

@@ -25,6 +25,7 @@ KDE_FP32, KDE_FP64 = 0, 1
 STATUS_NAMES = {0: "OK", 1: "INVALID", 2: "DEGENERATE", 3: "DOMAIN", 4: "OOM", 5: "CUDA",
                 6: "TIMEOUT", 7: "BUSY"}
 RESULT_FIELDS = ("mean", "sigma", "psi8", "g1", "psi6", "g2", "psi4", "h")
+STATIC_MAX_N = 65536   # KDE_STATIC_MAX_N
 
 
 class KdeResult(ctypes.Structure):
@@ -61,6 +62,7 @@ SIGNATURES = {
     "kde_plugin_h_f32": (_i32, [_vp, _i64, ctypes.c_int, _vp, _vp]),
     "kde_plugin_h_batch": (_i32, [_vp, _vp, _i64, ctypes.c_int, _vp, _vp]),
     "kde_psi_slots": (_i32, [_vp, _i64, ctypes.c_int, _d, ctypes.c_int, _vp, _i64, _vp]),
+    "kde_psi_static": (_i32, [_vp, _i64, ctypes.c_int, _d, ctypes.c_int, _vp, _vp]),
     "kde_server_create": (_i32, [_vp, _vp]),
     "kde_server_submit": (_i32, [_vp, _vp, _i64, ctypes.c_int, _vp]),
     "kde_server_poll": (_i32, [_vp, ctypes.c_uint64, _i32, _vp, _vp]),
@@ -171,6 +173,18 @@ def kde_psi(x, r: int, g: float, prec: int = KDE_FP32, out=None, stream=None):
     v = ctypes.c_double()
     st = load().kde_psi(p, n, int(r), float(g), int(prec), ctypes.addressof(v), _stream(stream))
     _check(st)
+    return v.value
+
+
+def kde_psi_static(x, r: int, g: float, prec: int = KDE_FP32, out=None, stream=None):
+    """psi_r(g) like kde_psi for n <= STATIC_MAX_N, in the library's fixed scratch
+    area (no device allocation).  Calls must not overlap on the device."""
+    p, n, keep = _buf(x, np.float64)
+    if out is not None:
+        _check(load().kde_psi_static(p, n, int(r), float(g), int(prec), out.data_ptr(), _stream(stream)))
+        return None
+    v = ctypes.c_double()
+    _check(load().kde_psi_static(p, n, int(r), float(g), int(prec), ctypes.addressof(v), _stream(stream)))
     return v.value
 
 
