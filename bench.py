@@ -12,6 +12,10 @@ n(n-1)/2 pairs, h.  The workload is n = 65536 values of the bimodal mixture
   roofline  the pair kernel (r = 6), timed live by events recorded around it
             inside the captured graph, against the FP32-issue / MUFU ALU bound.
   fp64      the all-binary64 GPU path on the same workload.
+  batch     512 samples, n log-uniform in [256, 262144], in one batched call.
+  serving   the first requests of the seeded served stream (n log-uniform in
+            [1000, 4194304], Poisson arrivals at 0.8 x the measured capacity)
+            replayed through the continuous-batching server: p50/p99 latency.
   cpu_baseline  the CPU oracle on this host's cores, one full run.
 
 `--impl reference` times the CPU oracle instead (the reference arm).
@@ -53,6 +57,11 @@ def parse():
     ap.add_argument("--n", type=int, default=N_DEFAULT)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-batch", action="store_true", help="skip the 512-sample batch leg")
+    ap.add_argument("--serve-requests", type=int, default=24,
+                    help="requests of the served stream to replay (0: skip the serving leg)")
+    ap.add_argument("--serve-load", type=float, default=0.8,
+                    help="arrival rate as a fraction of the measured FP32 capacity")
     return ap.parse_args()
 
 
@@ -141,17 +150,18 @@ class ClockSampler:
                 "samples": len(rows)}
 
 
-# Instructions per unique pair of the binary32 pair kernel (all issue on the
-# FP32/INT pipes, no MUFU):
-#   FADD  d = y_i - y_j (exact on the per-sample grid)
-#   FMUL  v = d^2 ;  FMNMX  clamp of v
+# Instructions per pair of the binary32 pair kernel on a tile pair that needs
+# no clamp (all issue on the FP32/INT pipes, no MUFU):
+#   FADD  d = y_i - y_j (exact on the per-sample grid) ;  FMUL  v = d^2
 #   FFMA + FADD + FFMA   k = round(t), f = t - k for t = -v c_hi
 #   8 FFMA   degree-8 polynomial for 2^f
 #   SHL + IADD   2^k into the exponent field
 #   r/2 FFMA   Horner for He_r on v (3 for He_6, 2 for He_4)
-#   FMUL   term ;  4 FADD   Kahan-compensated accumulation
-#   FMUL + FFMA   the c_lo part of the exponent, accumulated apart
-ISSUE_PER_PAIR = {6: 26, 4: 25}
+#   FMUL   term ;  FFMA   sum of term * v for the c_lo correction
+#   3/4 FADD + 4/4 FADD   groups of 4 terms, one Kahan step per group
+# Tile pairs that reach the clamp add one FMNMX.  The bound below uses the
+# smaller count, so it is the higher (stricter) roofline.
+ISSUE_PER_PAIR = {6: 21.75, 4: 20.75}
 KERNEL_SOURCE = os.path.join(os.path.dirname(os.path.abspath(__file__)),
                              "paper_1505_02100_gb300", "csrc", "kde_kernels.cu")
 TRAFFIC_FILE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "profiles",
@@ -182,6 +192,77 @@ def alu_peak(r: int, sms: int, f_mhz: float):
     """
     per_clk = 128.0 / ISSUE_PER_PAIR[r]
     return {"pairs_per_s": sms * f_mhz * 1e6 * per_clk, "pairs_per_clk_sm": per_clk}
+
+
+def batch_leg(kde, torch, dev, stream, flush, steps: int = 2, warmup: int = 1):
+    """512 samples, n log-uniform in [256, 262144] (normal, mixture or t3 each), one
+    kde_plugin_h_batch call per step, input resident on the device, FP32 pairs."""
+    import numpy as np
+
+    import synthdata
+    xs = [synthdata.sample_from_spec(s) for s in synthdata.batch_specs()]
+    ns = np.array([x.size for x in xs], dtype=np.int64)
+    off = np.concatenate([[0], np.cumsum(ns)])
+    xd = torch.tensor(np.concatenate(xs), dtype=torch.float64, device=dev)
+    m = len(xs)
+    out = torch.empty(m * kde.RESULT_BYTES // 8, dtype=torch.float64, device=dev)
+    for _ in range(warmup):
+        kde.kde_plugin_h_batch(xd, off, kde.KDE_FP32, out=out, stream=stream)
+    ms = []
+    for _ in range(steps):
+        with torch.cuda.stream(stream):
+            flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        kde.kde_plugin_h_batch(xd, off, kde.KDE_FP32, out=out, stream=stream)
+        e1.record(stream)
+        stream.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    res = out.cpu().numpy().view(np.int32).reshape(m, kde.RESULT_BYTES // 4)
+    ok = int((res[:, 16] == 0).sum())
+    t = statistics.mean(ms) / 1e3
+    pairs = int((ns * (ns - 1)).sum())          # psi6 + psi4: 2 x n(n-1)/2 per sample
+    return {"samples": m, "n_total": int(ns.sum()), "pair_evals": pairs, "ms": 1e3 * t,
+            "pair_evals_per_s": pairs / t, "bandwidths_per_s": m / t, "status_ok": ok,
+            "steps": steps, "input": "device-resident binary64, L2 flushed before each step"}
+
+
+def serve_leg(kde, capacity: float, count: int, load: float):
+    """The first `count` requests of the served stream (n log-uniform in [1000, 4194304],
+    FP32 samples, Poisson arrivals at `load` x the measured FP32 capacity), replayed in
+    real time through the continuous-batching server."""
+    import numpy as np
+
+    import synthdata
+    specs = synthdata.server_specs(count)
+    xs = [synthdata.sample_from_spec(s, np.float32) for s in specs]
+    lo, hi = 1000.0, 4194304.0
+    e_pairs = (hi * hi - lo * lo) / (2.0 * math.log(hi / lo))     # E[n^2] ~ E[n(n-1)], log-uniform n
+    rate = load * capacity / e_pairs
+    arrivals = synthdata.poisson_arrivals(count, rate)
+    with kde.Server(hbm_budget_bytes=24 << 30, max_inflight=256) as srv:
+        t0 = time.perf_counter()
+        tickets = []
+        for k, x in enumerate(xs):
+            wait = t0 + arrivals[k] - time.perf_counter()
+            if wait > 0:
+                time.sleep(wait)
+            tickets.append(srv.submit(x, kde.KDE_FP32))
+        got = [srv.poll(t, timeout_ms=600000) for t in tickets]
+    lat, queue, ok, pairs = [], [], 0, 0
+    for (res, tm), x in zip(got, xs):
+        ok += int(res["status"] == 0)
+        lat.append((tm["t_done_ns"] - tm["t_submit_ns"]) / 1e6)
+        queue.append((tm["t_admit_ns"] - tm["t_submit_ns"]) / 1e6)
+        pairs += x.size * (x.size - 1)
+    span = (max(tm["t_done_ns"] for _, tm in got) - min(tm["t_submit_ns"] for _, tm in got)) / 1e9
+    return {"requests": count, "arrival_rate_per_s": rate, "load": load, "status_ok": ok,
+            "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
+                           "max": float(max(lat))},
+            "admit_wait_ms_p50": float(np.percentile(queue, 50)),
+            "pair_evals_per_s": pairs / span, "n_sizes": [int(x.size) for x in xs],
+            "sample": f"first {count} of the seeded 10000-request stream"}
+
 
 
 def run_reference(args, ws, rank):
@@ -297,6 +378,12 @@ def run_ours(args, ws, rank, local):
                 "pairs6_ms": statistics.mean(k6_64), "pairs4_ms": statistics.mean(k4_64),
                 "h": res64["h"]}
 
+    batch = serve = None
+    if ws == 1 and not args.no_batch:
+        batch = batch_leg(kde, torch, dev, stream, flush)
+    if ws == 1 and args.serve_requests > 0:
+        serve = serve_leg(kde, value, args.serve_requests, args.serve_load)
+
     if rank != 0:
         return
     with ClockSampler(local) as pclk:
@@ -346,6 +433,12 @@ def run_ours(args, ws, rank, local):
     if fp64:
         line["fp64"] = fp64
         line["fp32_over_fp64"] = value / fp64["value"]
+    if batch:
+        line["batch"] = batch
+        if fp64:
+            line["batch"]["fp32_batch_over_fp64_single"] = batch["pair_evals_per_s"] / fp64["value"]
+    if serve:
+        line["serving"] = serve
     if not args.no_cpu_baseline:
         import oracle
         cores = oracle.default_threads()

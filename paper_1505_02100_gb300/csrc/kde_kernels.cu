@@ -344,11 +344,11 @@ struct Coef {
 // The c_lo factor is not applied to f or to the term: there it would be a
 // smooth correction a few units in the last place, added to a value already
 // on the binary32 grid, and rounding would drop the same fraction of it from
-// every term -- a bias.  Instead the caller accumulates -term * (v c_lo ln 2)
-// in a separate binary32 sum per row (`corr`, one FFMA per pair), and adds
-// those sums to a binary64 total of its own.  (Folding them into the Kahan
-// sum does not work: its compensation term keeps only the bits above half an
-// ulp of the next, much larger, partial sum added to it.)
+// every term -- a bias.  Instead the caller sums term * v per row in binary32
+// (one FFMA per pair) and subtracts c_lo ln 2 times that sum, in binary64,
+// from a correction total of its own.  (Folding it into the Kahan sum does
+// not work: the compensation term keeps only the bits above half an ulp of
+// the next, much larger, partial sum added to it.)
 //
 // The pair sum cancels so strongly (sum |terms| / |sum| ~ 2e4 for psi6 at
 // n = 2^20, growing like (sigma/g)^6) that any bias of the exponential at the
@@ -359,7 +359,8 @@ struct Coef {
 // reduction whose last step rounds a value on a grid coarser than its result
 // (t - k ln2_hi with t large) ~8e-6 on psi6.
 // u^2 is clamped to 125 * 2 ln 2 (~173): beyond it every term is below 1e-31,
-// the exponent stays normal and He_r stays finite.
+// the exponent stays normal and He_r stays finite.  Tile pairs whose largest
+// distance is below the clamp skip it (CLAMP = false).
 constexpr float kRoundMagic = 12582912.0f;                 // 1.5 * 2^23
 constexpr double kInvTwoLn2 = 0.72134752044448170367996234050095;
 constexpr float kMinT = 125.0f;
@@ -378,12 +379,12 @@ __device__ __forceinline__ float exp2_reduced(float f) {
 
 // One pair term, binary32, without its 2^(-v c_lo) factor: a, b scaled values
 // (grid units); c_hi = 2^(-2F) / (2 ln 2) rounded; vmax = kMinT / c_hi.
-// `dl` receives v c_lo ln 2, the relative amount by which the term is too large.
-template <int RORD>
+// `vout` receives v: the term is too large by the relative amount v c_lo ln 2.
+template <int RORD, bool CLAMP>
 __device__ __forceinline__ float term32(float a, float b, const Coef<float, RORD>& cf, float c_hi,
-                                        float c_lo_ln2, float vmax, float& dl) {
+                                        float vmax, float& vout) {
   const float d = __fsub_rn(a, b);                        // exact (see kde_internal.cuh)
-  const float v = fminf(__fmul_rn(d, d), vmax);           // u^2 * 2^(2F)
+  const float v = CLAMP ? fminf(__fmul_rn(d, d), vmax) : __fmul_rn(d, d);
   const float yb = __fmaf_rn(v, -c_hi, kRoundMagic);      // low bits: k = round(t)
   const float kf = __fsub_rn(yb, kRoundMagic);
   const float f = __fmaf_rn(v, -c_hi, -kf);               // t - k (c_hi part)
@@ -391,7 +392,7 @@ __device__ __forceinline__ float term32(float a, float b, const Coef<float, RORD
   float p;
   if (RORD == 6) p = __fmaf_rn(__fmaf_rn(__fmaf_rn(cf.c3, v, cf.c2), v, cf.c1), v, cf.c0);
   else p = __fmaf_rn(__fmaf_rn(cf.c2, v, cf.c1), v, cf.c0);
-  dl = __fmul_rn(v, c_lo_ln2);
+  vout = v;
   return __fmul_rn(p, e);
 }
 
@@ -421,25 +422,21 @@ struct Kahan32 {
 };
 
 // One tile pair, FP32: this thread's ROWS rows against the TILE columns in
-// shared memory, into ROWS x CJ independent (instruction-level parallel)
-// Kahan-compensated sums, folded into the thread's running Kahan sum once per
-// tile pair, plus one c_lo correction sum per row (see term32), added to the
-// thread's binary64 correction total `cacc`.  Sorted tiles
-// make the terms one accumulator sees nearly equal; plain binary32 summation
-// of such runs drifts systematically, which the cancellation of the pair sum
-// would amplify.
-template <int RORD, int ROWS, int CJ, int TILE>
+// shared memory.  Per row, each group of 4 terms (one float4 of columns) is
+// summed as a tree and added to the row's Kahan-compensated sum; the row sums
+// are folded into the thread's running Kahan sum once per tile pair.  Sorted
+// tiles make the terms one accumulator sees nearly equal; plain binary32
+// summation of such runs drifts systematically, which the cancellation of the
+// pair sum would amplify.  Per row, sum(term * v) feeds the c_lo correction
+// (see term32), which goes to the thread's binary64 total `cacc`.
+template <int RORD, int ROWS, int CJ, int TILE, bool CLAMP>
 __device__ __forceinline__ void tile_pass(const float* __restrict__ tile, const float (&w)[ROWS],
-                                          const Coef<float, RORD>& cf, float c_hi, float c_lo_ln2,
+                                          const Coef<float, RORD>& cf, float c_hi, double c_lo_ln2,
                                           float vmax, Kahan32& acc, double& cacc) {
-  static_assert(CJ % 4 == 0, "column groups are float4 loads");
-  float sum[ROWS][CJ], comp[ROWS][CJ], corr[ROWS];
+  static_assert(CJ == 4, "one float4 of columns per group of terms");
+  float sum[ROWS], comp[ROWS], tv[ROWS];
 #pragma unroll
-  for (int r = 0; r < ROWS; ++r) {
-    corr[r] = 0.0f;
-#pragma unroll
-    for (int q = 0; q < CJ; ++q) sum[r][q] = comp[r][q] = 0.0f;
-  }
+  for (int r = 0; r < ROWS; ++r) sum[r] = comp[r] = tv[r] = 0.0f;
 #pragma unroll 1
   for (int jj = 0; jj < TILE; jj += CJ) {
     float b[CJ];
@@ -449,24 +446,28 @@ __device__ __forceinline__ void tile_pass(const float* __restrict__ tile, const 
       b[q4] = v4.x; b[q4 + 1] = v4.y; b[q4 + 2] = v4.z; b[q4 + 3] = v4.w;
     }
 #pragma unroll
-    for (int r = 0; r < ROWS; ++r)
+    for (int r = 0; r < ROWS; ++r) {
+      float t[CJ];
 #pragma unroll
       for (int q = 0; q < CJ; ++q) {
-        float dl;
-        const float term = term32<RORD>(w[r], b[q], cf, c_hi, c_lo_ln2, vmax, dl);
-        corr[r] = __fmaf_rn(term, -dl, corr[r]);
-        const float y = __fsub_rn(term, comp[r][q]);
-        const float t = __fadd_rn(sum[r][q], y);
-        comp[r][q] = __fsub_rn(__fsub_rn(t, sum[r][q]), y);
-        sum[r][q] = t;
+        float v;
+        t[q] = term32<RORD, CLAMP>(w[r], b[q], cf, c_hi, vmax, v);
+        tv[r] = __fmaf_rn(t[q], v, tv[r]);
       }
+      const float g4 = __fadd_rn(__fadd_rn(t[0], t[1]), __fadd_rn(t[2], t[3]));
+      const float y = __fsub_rn(g4, comp[r]);
+      const float tt = __fadd_rn(sum[r], y);
+      comp[r] = __fsub_rn(__fsub_rn(tt, sum[r]), y);
+      sum[r] = tt;
+    }
   }
+  float tvsum = 0.0f;
 #pragma unroll
   for (int r = 0; r < ROWS; ++r) {
-#pragma unroll
-    for (int q = 0; q < CJ; ++q) acc.add(__fsub_rn(sum[r][q], comp[r][q]));
-    cacc += static_cast<double>(corr[r]);
+    acc.add(__fsub_rn(sum[r], comp[r]));
+    tvsum = __fadd_rn(tvsum, tv[r]);
   }
+  cacc -= static_cast<double>(tvsum) * c_lo_ln2;
 }
 
 // One tile pair, FP64 (plain binary64 accumulation, accurate exp).
@@ -570,8 +571,7 @@ __global__ void __launch_bounds__(THREADS) pairs_kernel(PairArgs a) {
       const T pad_lo = static_cast<T>(st->pad_lo), pad_hi = static_cast<T>(st->pad_hi);
       const double p2 = ldexp(1.0, -2 * st->F);
       const float c_hi = static_cast<float>(kInvTwoLn2 * p2);
-      const float c_lo_ln2 =
-          static_cast<float>((kInvTwoLn2 * p2 - static_cast<double>(c_hi)) * 0.69314718055994530942);
+      const double c_lo_ln2 = (kInvTwoLn2 * p2 - static_cast<double>(c_hi)) * 0.69314718055994530942;
       const float vmax = kMinT / c_hi;
       Coef<T, RORD> full, half;
       full.set(1.0, p2);
@@ -607,7 +607,12 @@ __global__ void __launch_bounds__(THREADS) pairs_kernel(PairArgs a) {
         const bool diag = (I == J);
         const Coef<T, RORD>& cf = diag ? half : full;
         if constexpr (PREC == KDE_FP32) {
-          tile_pass<RORD, ROWS, CJ, TILE>(tile, w, cf, c_hi, c_lo_ln2, vmax, acc32, cacc);
+          // The sample is sorted, so the largest |y_i - y_j| of the tile pair is
+          // its last column minus its first row; tiles with padding always clamp.
+          const double span = static_cast<double>(tile[TILE - 1]) - static_cast<double>(y[I * TILE]);
+          const bool near = (J + 1) * TILE <= d.n && span * span <= static_cast<double>(vmax);
+          if (near) tile_pass<RORD, ROWS, CJ, TILE, false>(tile, w, cf, c_hi, c_lo_ln2, vmax, acc32, cacc);
+          else tile_pass<RORD, ROWS, CJ, TILE, true>(tile, w, cf, c_hi, c_lo_ln2, vmax, acc32, cacc);
         } else {
           tile_pass64<RORD, ROWS, TILE>(tile, w, cf, acc64);
         }
