@@ -168,17 +168,20 @@ TRAFFIC_FILE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "profile
                             "pairs_kernel_r6_bimodal_n65536.md")
 
 
-def measured_traffic():
+def measured_traffic(tile_config: int):
     """DRAM bytes per launch of the r = 6 pair kernel from the committed ncu summary,
-    or None when the kernel source changed since those counters were taken."""
+    or None when the kernel source or its tile configuration differ from the ones
+    those counters were taken with."""
     import hashlib
     try:
         text = open(TRAFFIC_FILE).read()
     except OSError:
         return None
-    fields = dict(re.findall(r"^- (kernel_source_sha256|dram_bytes_per_launch): `([^`]+)`", text, re.M))
+    fields = dict(re.findall(r"^- (kernel_source_sha256|dram_bytes_per_launch|tile_config): `([^`]+)`",
+                             text, re.M))
     digest = hashlib.sha256(open(KERNEL_SOURCE, "rb").read()).hexdigest()
-    if fields.get("kernel_source_sha256") != digest or "dram_bytes_per_launch" not in fields:
+    if (fields.get("kernel_source_sha256") != digest or "dram_bytes_per_launch" not in fields
+            or fields.get("tile_config") != str(tile_config)):
         return None
     return float(fields["dram_bytes_per_launch"])
 
@@ -308,6 +311,7 @@ def run_ours(args, ws, rank, local):
         kbuild.build()
     barrier(ws)
     kde.load()
+    tuned = kde.kde_autotune(kde.KDE_FP32)     # tile configuration per size class, this device
     n = args.n
     x = workload(n)
     xd = torch.tensor(x, dtype=torch.float64, device=dev)
@@ -407,13 +411,16 @@ def run_ours(args, ws, rank, local):
         "config": {"workload": WORKLOAD, "n": n, "distribution": "0.5N(-1,0.5^2)+0.5N(1,0.5^2)+1e4",
                    "precision": "fp32 pair terms, fp64 moments/reductions/scalars",
                    "l2": "flushed between steps (512 MiB write outside the timed events)",
-                   "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU"},
+                   "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU",
+                   "tile_configs": {"tuned_per_class": tuned,
+                                    "this_n": list(kde.kde_tile_config(n, kde.KDE_FP32))}},
         "gpu_launches": int(sum(launches)),
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 8 * n,
                 "d2h_bytes_per_step": kde.RESULT_BYTES},
         "roofline": {"bound": "alu", "kernel": "pairs_kernel r=6 (Step IV)",
                      "achieved": achieved / 1e9, "peak": peak["pairs_per_s"] / 1e9, "unit": "Gpair/s",
-                     "frac": achieved / peak["pairs_per_s"], "traffic": measured_traffic(),
+                     "frac": achieved / peak["pairs_per_s"],
+                     "traffic": measured_traffic(kde.kde_tile_config(n, kde.KDE_FP32)[0]),
                      "peak_basis": f"{sms} SMs x 2070 MHz x 128 issue slots / {ISSUE_PER_PAIR[6]} "
                                    f"instructions per pair = {peak['pairs_per_clk_sm']:.2f} pairs/clk/SM",
                      "pairs4_kernel": {"ms": statistics.mean(k4),

@@ -148,6 +148,34 @@ KDE_API kde_status kde_plugin_h_batch(const double* x_packed, const int64_t* off
 KDE_API kde_status kde_psi_slots(const double* x, int64_t n, int r, double g, kde_precision prec,
                          double* slots, int64_t cap, int64_t* info);
 
+/* ---- tile-configuration autotuner -------------------------------------------- */
+
+/*
+ * kde_autotune -- time every tile configuration of the pair kernel for `prec`
+ * on the current device and use the fastest per size class from now on.  The
+ * paper has no counterpart (its design is a fixed FPGA pipeline).  Each
+ * configuration runs psi_6 (Step IV) on synthetic normal samples of n = 2^10,
+ * 2^12, 2^14, 2^16 and 2^18 (device-resident, best of 3 after a warm-up); the
+ * fastest is recorded for the size class n in [2^(k-1), 2^(k+1)) around each,
+ * and 2^18 also serves every larger n.  The built-in choice is kept unless
+ * another configuration is at least 3% faster.  Every later plan on this device
+ * (kde_psi, kde_plugin_h, batch, server, static) consults the table.
+ *   chosen  host int32[cap], cap >= 5, or NULL: the configuration index chosen
+ *           for each size class, smallest first.
+ * Tuning allocates a few MB of device memory and takes about a second for
+ * KDE_FP32 (several seconds for KDE_FP64).  Results computed with another
+ * configuration may differ in the last bits (within the stated tolerance).
+ * Environment KDE_FP32_TILE_CONFIG / KDE_FP64_TILE_CONFIG still take priority.
+ */
+KDE_API kde_status kde_autotune(kde_precision prec, int32_t* chosen, int cap);
+/* Forget the tuned table of `prec` on the current device: the built-in rule
+ * applies again. */
+KDE_API kde_status kde_autotune_clear(kde_precision prec);
+/* The tile configuration a plan for n values of `prec` uses now on the current
+ * device: info[0] configuration index, info[1] threads per block, info[2] rows
+ * per thread (tile side T = threads x rows).  host int32[3]. */
+KDE_API kde_status kde_tile_config(kde_precision prec, int64_t n, int32_t* info);
+
 /* ---- allocation-free variant ---------------------------------------------------- */
 
 /* Largest n kde_psi_static accepts. */

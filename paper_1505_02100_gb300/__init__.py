@@ -63,6 +63,9 @@ SIGNATURES = {
     "kde_plugin_h_batch": (_i32, [_vp, _vp, _i64, ctypes.c_int, _vp, _vp]),
     "kde_psi_slots": (_i32, [_vp, _i64, ctypes.c_int, _d, ctypes.c_int, _vp, _i64, _vp]),
     "kde_psi_static": (_i32, [_vp, _i64, ctypes.c_int, _d, ctypes.c_int, _vp, _vp]),
+    "kde_autotune": (_i32, [ctypes.c_int, _vp, ctypes.c_int]),
+    "kde_autotune_clear": (_i32, [ctypes.c_int]),
+    "kde_tile_config": (_i32, [ctypes.c_int, _i64, _vp]),
     "kde_server_create": (_i32, [_vp, _vp]),
     "kde_server_submit": (_i32, [_vp, _vp, _i64, ctypes.c_int, _vp]),
     "kde_server_poll": (_i32, [_vp, ctypes.c_uint64, _i32, _vp, _vp]),
@@ -174,6 +177,26 @@ def kde_psi(x, r: int, g: float, prec: int = KDE_FP32, out=None, stream=None):
     st = load().kde_psi(p, n, int(r), float(g), int(prec), ctypes.addressof(v), _stream(stream))
     _check(st)
     return v.value
+
+
+def kde_autotune(prec: int = KDE_FP32):
+    """Time every pair-kernel tile configuration on this device; the fastest per
+    size class is used from now on.  Returns the chosen configuration per class
+    (n = 2^10, 2^12, 2^14, 2^16, 2^18 and above)."""
+    out = (ctypes.c_int32 * 5)()
+    _check(load().kde_autotune(int(prec), ctypes.addressof(out), 5))
+    return list(out)
+
+
+def kde_autotune_clear(prec: int = KDE_FP32) -> None:
+    _check(load().kde_autotune_clear(int(prec)))
+
+
+def kde_tile_config(n: int, prec: int = KDE_FP32):
+    """(configuration index, threads per block, rows per thread) a plan for n uses now."""
+    out = (ctypes.c_int32 * 3)()
+    _check(load().kde_tile_config(int(prec), int(n), ctypes.addressof(out)))
+    return tuple(out)
 
 
 def kde_psi_static(x, r: int, g: float, prec: int = KDE_FP32, out=None, stream=None):

@@ -68,9 +68,16 @@ int env_int(const char* name, int dflt) {
 // result -- alone, in a batch or in the server.
 int choose_config(int prec, int64_t n) {
   const int count = pair_config_count(prec);
+  if (t_tune_force_cfg >= 0 && t_tune_force_cfg < count) return t_tune_force_cfg;   // the tuner is timing it
   const int forced = env_int(prec == KDE_FP32 ? "KDE_FP32_TILE_CONFIG" : "KDE_FP64_TILE_CONFIG", -1);
   if (forced >= 0 && forced < count) return forced;
-  if (prec == KDE_FP32) return n <= 16384 ? 3 : 0;   // T = 256 for small n, else T = 512 (32 classes)
+  const int tuned = tuned_config(prec, n);
+  if (tuned >= 0 && tuned < count) return tuned;
+  return default_config(prec, n);
+}
+
+int default_config(int prec, int64_t n) {
+  if (prec == KDE_FP32) return n <= 16384 ? 3 : 0;   // T = 256 for small n, else T = 512
   return 0;                                          // T = 256
 }
 
@@ -277,6 +284,24 @@ kde_status get_workspace(cudaStream_t stream, Workspace** out) {
   }
   *out = slot.get();
   return KDE_OK;
+}
+
+// Release and forget the workspace of (current device, stream).
+void drop_workspace(cudaStream_t stream) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    cudaGetLastError();
+    return;
+  }
+  Registry& R = registry();
+  std::lock_guard<std::mutex> lk(R.mu);
+  auto it = R.ws.find({dev, stream});
+  if (it == R.ws.end()) return;
+  {
+    std::lock_guard<std::mutex> wl(it->second->mu);
+    it->second->release();
+  }
+  R.ws.erase(it);
 }
 
 // Grow `b` to at least `bytes`.  Growing frees the old buffer, so in-flight

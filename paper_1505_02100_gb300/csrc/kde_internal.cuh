@@ -153,7 +153,13 @@ int pair_blocks_per_sm(int prec, int cfg);
 kde_status set_err(kde_status s, const std::string& m);
 bool is_device_ptr(const void* p);
 int num_sms();
-int choose_config(int prec, int64_t n);
+int choose_config(int prec, int64_t n);    // tuner's force, environment, tuned table, built-in rule
+int default_config(int prec, int64_t n);   // the built-in rule
 SampleDesc make_desc(int prec, int cfg, int64_t n, double g_fixed);
+void drop_workspace(cudaStream_t stream);
+
+// tile-configuration autotuner (kde_tune.cu)
+extern thread_local int t_tune_force_cfg;    // >= 0 only while the tuner times that configuration
+int tuned_config(int prec, int64_t n);       // tuned choice for the current device, or -1
 
 }  // namespace kde

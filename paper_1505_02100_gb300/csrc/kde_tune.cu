@@ -1,0 +1,195 @@
+// kde_tune.cu -- autotuner of the pair kernel's tile configuration.
+//
+// Every configuration (threads x rows per thread = tile side T) computes the
+// same functional; they differ in occupancy, instruction-level parallelism and
+// in how evenly a sample's tile pairs spread over the SMs, which depends on n.
+// kde_autotune times each configuration through the ordinary psi_r path, on
+// synthetic normal samples of n = 2^10, 2^12, ..., 2^18 with device-resident
+// input and output, and records the fastest per size class for the current
+// device (the built-in choice stays unless another is at least 3% faster).
+// From then on every plan (single, batch, server, static) picks its
+// configuration from that table.  Sizes above 2^18 use the 2^18 choice: by
+// then every SM holds many tile pairs and only the per-pair cost matters.
+//
+// A different configuration sums the pairs in a different order, so results
+// may change in the last bits after tuning (always within the stated
+// tolerance); without tuning, the built-in rule applies and results are
+// reproducible bit for bit.
+#include "kde_internal.cuh"
+
+#include <algorithm>
+#include <cmath>
+#include <mutex>
+#include <vector>
+
+namespace kde {
+
+thread_local int t_tune_force_cfg = -1;
+
+namespace {
+
+constexpr int kTuneLog2[] = {10, 12, 14, 16, 18};
+constexpr int kTuneBuckets = sizeof(kTuneLog2) / sizeof(kTuneLog2[0]);
+constexpr int kTuneDevices = 64;
+constexpr float kTuneMargin = 0.03f;   // another configuration must be >= 3% faster
+
+std::mutex g_tune_mu;
+int g_tuned[kTuneDevices][2][kTuneBuckets];   // -1: not tuned
+bool g_tuned_init = false;
+
+void init_table_locked() {
+  if (g_tuned_init) return;
+  for (auto& d : g_tuned)
+    for (auto& p : d)
+      for (int& c : p) c = -1;
+  g_tuned_init = true;
+}
+
+int bucket_of(int64_t n) {
+  // nearest tuned size class in log2
+  const double l = std::log2(static_cast<double>(n > 1 ? n : 2));
+  int best = 0;
+  for (int b = 1; b < kTuneBuckets; ++b)
+    if (std::fabs(l - kTuneLog2[b]) < std::fabs(l - kTuneLog2[best])) best = b;
+  return best;
+}
+
+// SplitMix64 stream -> standard normals (Box-Muller); only for timing inputs.
+void normal_sample(std::vector<double>& x, uint64_t seed) {
+  uint64_t s = seed;
+  auto next = [&s]() {
+    uint64_t z = (s += 0x9E3779B97F4A7C15ull);
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+  };
+  for (size_t i = 0; i < x.size(); i += 2) {
+    const double u1 = (static_cast<double>(next() >> 11) + 0.5) * 0x1.0p-53;
+    const double u2 = (static_cast<double>(next() >> 11) + 0.5) * 0x1.0p-53;
+    const double r = std::sqrt(-2.0 * std::log(u1));
+    x[i] = r * std::cos(2.0 * kPi * u2);
+    if (i + 1 < x.size()) x[i + 1] = r * std::sin(2.0 * kPi * u2);
+  }
+}
+
+}  // namespace
+
+int tuned_config(int prec, int64_t n) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kTuneDevices) {
+    cudaGetLastError();
+    return -1;
+  }
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  init_table_locked();
+  return g_tuned[dev][prec == KDE_FP32 ? 0 : 1][bucket_of(n)];
+}
+
+}  // namespace kde
+
+using namespace kde;
+
+extern "C" kde_status kde_autotune(kde_precision prec, int32_t* chosen, int cap) {
+  if (prec != KDE_FP32 && prec != KDE_FP64) return set_err(KDE_ERR_INVALID, "bad precision");
+  if (chosen && cap < kTuneBuckets) return set_err(KDE_ERR_INVALID, "need room for 5 configurations");
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kTuneDevices) {
+    cudaGetLastError();
+    return set_err(KDE_ERR_CUDA, "no usable current device");
+  }
+  const int count = pair_config_count(prec);
+  const int64_t nmax = int64_t(1) << kTuneLog2[kTuneBuckets - 1];
+  std::vector<double> host(static_cast<size_t>(nmax));
+  normal_sample(host, 0x5EEDull);
+  double* xd = nullptr;
+  double* outd = nullptr;
+  cudaStream_t s = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  kde_status st = KDE_OK;
+  auto cu = [&](cudaError_t e, const char* what) {
+    if (e != cudaSuccess && st == KDE_OK) st = set_err(KDE_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+    return e == cudaSuccess;
+  };
+  if (cu(cudaMalloc(&xd, host.size() * sizeof(double)), "tuning buffer") &&
+      cu(cudaMalloc(&outd, sizeof(double)), "tuning output") &&
+      cu(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking), "tuning stream") &&
+      cu(cudaEventCreate(&e0), "event") && cu(cudaEventCreate(&e1), "event") &&
+      cu(cudaMemcpy(xd, host.data(), host.size() * sizeof(double), cudaMemcpyHostToDevice), "copy")) {
+    int best_cfg[kTuneBuckets];
+    for (int b = 0; b < kTuneBuckets && st == KDE_OK; ++b) {
+      const int64_t n = int64_t(1) << kTuneLog2[b];
+      // normal-reference g1 for sigma = 1 (Steps II-III)
+      const double psi8 = 105.0 / (32.0 * std::sqrt(kPi));
+      const double g = std::pow(30.0 / std::sqrt(2.0 * kPi) / (psi8 * static_cast<double>(n)), 1.0 / 9.0);
+      std::vector<float> ms_cfg(static_cast<size_t>(count), 1e30f);
+      for (int c = 0; c < count && st == KDE_OK; ++c) {
+        t_tune_force_cfg = c;
+        float ms_best = 1e30f;
+        for (int rep = 0; rep < 4 && st == KDE_OK; ++rep) {   // first one warms up (and captures the graph)
+          cu(cudaEventRecord(e0, s), "record");
+          kde_status ps = kde_psi(xd, n, 6, g, prec, outd, s);
+          if (ps != KDE_OK) st = ps;
+          cu(cudaEventRecord(e1, s), "record");
+          cu(cudaEventSynchronize(e1), "sync");
+          float ms = 0.0f;
+          cu(cudaEventElapsedTime(&ms, e0, e1), "elapsed");
+          if (rep > 0) ms_best = std::min(ms_best, ms);
+        }
+        t_tune_force_cfg = -1;
+        ms_cfg[static_cast<size_t>(c)] = ms_best;
+      }
+      // keep the built-in choice unless another configuration is clearly
+      // faster: the table then changes results only where it pays
+      const int dflt = default_config(prec, n);
+      int pick = dflt;
+      for (int c = 0; c < count; ++c)
+        if (ms_cfg[static_cast<size_t>(c)] < ms_cfg[static_cast<size_t>(pick)]) pick = c;
+      if (ms_cfg[static_cast<size_t>(pick)] > (1.0f - kTuneMargin) * ms_cfg[static_cast<size_t>(dflt)]) pick = dflt;
+      best_cfg[b] = pick;
+    }
+    t_tune_force_cfg = -1;
+    if (st == KDE_OK) {
+      std::lock_guard<std::mutex> lk(g_tune_mu);
+      init_table_locked();
+      for (int b = 0; b < kTuneBuckets; ++b) {
+        g_tuned[dev][prec == KDE_FP32 ? 0 : 1][b] = best_cfg[b];
+        if (chosen) chosen[b] = best_cfg[b];
+      }
+    }
+  }
+  if (s) {
+    cudaStreamSynchronize(s);
+    drop_workspace(s);
+  }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  if (s) cudaStreamDestroy(s);
+  if (outd) cudaFree(outd);
+  if (xd) cudaFree(xd);
+  return st;
+}
+
+extern "C" kde_status kde_autotune_clear(kde_precision prec) {
+  if (prec != KDE_FP32 && prec != KDE_FP64) return set_err(KDE_ERR_INVALID, "bad precision");
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kTuneDevices) {
+    cudaGetLastError();
+    return set_err(KDE_ERR_CUDA, "no usable current device");
+  }
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  init_table_locked();
+  for (int& c : g_tuned[dev][prec == KDE_FP32 ? 0 : 1]) c = -1;
+  return KDE_OK;
+}
+
+extern "C" kde_status kde_tile_config(kde_precision prec, int64_t n, int32_t* info) {
+  if (!info) return set_err(KDE_ERR_INVALID, "null pointer");
+  if (prec != KDE_FP32 && prec != KDE_FP64) return set_err(KDE_ERR_INVALID, "bad precision");
+  if (n < 2) return set_err(KDE_ERR_INVALID, "n < 2");
+  const int cfg = choose_config(prec, n);
+  const PairConfig pc = pair_config(prec, cfg);
+  info[0] = cfg;
+  info[1] = pc.threads;
+  info[2] = pc.rows;
+  return KDE_OK;
+}
