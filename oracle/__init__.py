@@ -75,6 +75,7 @@ def _load():
         lib.oracle_psi_ld.argtypes = [dp, i64, ip, ctypes.c_longdouble,
                                       ctypes.POINTER(ctypes.c_longdouble)]
         lib.oracle_long_double_mantissa_bits.restype = ip
+        lib.oracle_kde_eval.argtypes = [dp, i64, d, dp, i64, ip, dp]
         _lib = lib
     return _lib
 
@@ -159,3 +160,15 @@ def psi_ld(x, r: int, g: float) -> float:
 
 def long_double_bits() -> int:
     return _load().oracle_long_double_mantissa_bits()
+
+
+def kde_eval(x, h: float, points, threads: int | None = None) -> np.ndarray:
+    """Eq. (1) with the Gaussian kernel (Eq. 2): fhat(t) = (1/(n h)) sum_i K((t - X_i)/h)
+    at every point t."""
+    a, t = _arr(x), _arr(points).reshape(-1)
+    out = np.empty(t.size, dtype=np.float64)
+    st = _load().oracle_kde_eval(_ptr(a), a.size, float(h), _ptr(t), t.size,
+                                 int(threads or default_threads()), _ptr(out))
+    if st != OK:
+        raise ValueError(f"oracle_kde_eval status {st}")
+    return out

@@ -252,3 +252,49 @@ int oracle_plugin_ld(const double* x, int64_t n, oracle_result_ld* out) {
     out->status = ORACLE_OK;
     return ORACLE_OK;
 }
+
+/* ---- Eq. (1) with the Gaussian kernel of Eq. (2): the density estimate -------- */
+/* fhat(t_j) = (1 / (n h)) sum_i K((t_j - X_i) / h), one compensated sum per point. */
+typedef struct {
+    const double* x;
+    int64_t n;
+    double h;
+    const double* t;
+    int64_t m;
+    double* out;
+    int64_t next;
+} eval_job;
+
+static void* eval_worker(void* arg) {
+    eval_job* jb = (eval_job*)arg;
+    for (;;) {
+        int64_t j = __atomic_fetch_add(&jb->next, 1, __ATOMIC_RELAXED);
+        if (j >= jb->m) break;
+        csum acc = {0, 0};
+        for (int64_t i = 0; i < jb->n; ++i) {
+            double u = (jb->t[j] - jb->x[i]) / jb->h;
+            csum_add(&acc, inv_sqrt_2pi() * exp(-0.5 * u * u));
+        }
+        jb->out[j] = csum_value(&acc) / ((double)jb->n * jb->h);
+    }
+    return NULL;
+}
+
+int oracle_kde_eval(const double* x, int64_t n, double h, const double* t, int64_t m,
+                    int nthreads, double* out) {
+    if (!x || !t || !out || n < 1 || m < 0 || !(h > 0) || !isfinite(h)) return ORACLE_ERR_INVALID;
+    eval_job jb = {x, n, h, t, m, out, 0};
+    if (nthreads < 1) nthreads = 1;
+    if (nthreads > 1024) nthreads = 1024;
+    if (nthreads == 1 || m < 2) {
+        eval_worker(&jb);
+    } else {
+        pthread_t th[1024];
+        int started = 0;
+        for (int k = 0; k < nthreads; ++k)
+            if (pthread_create(&th[k], NULL, eval_worker, &jb) == 0) ++started;
+        if (started == 0) eval_worker(&jb);
+        for (int k = 0; k < started; ++k) pthread_join(th[k], NULL);
+    }
+    return ORACLE_OK;
+}

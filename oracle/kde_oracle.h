@@ -66,6 +66,12 @@ int oracle_plugin_ld(const double* x, int64_t n, oracle_result_ld* out);
 int oracle_psi_ld(const double* x, int64_t n, int r, long double g, long double* psi);
 int oracle_long_double_mantissa_bits(void);
 
+/* Eq. (1) with the Gaussian kernel of Eq. (2): fhat(t_j) = (1/(n h)) sum_i
+ * K((t_j - X_i)/h) for j < m, into out[j].  Threads over points; per-point
+ * compensated sums, so the bits do not depend on the thread count. */
+int oracle_kde_eval(const double* x, int64_t n, double h, const double* t, int64_t m,
+                    int nthreads, double* out);
+
 #ifdef __cplusplus
 }
 #endif
