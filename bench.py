@@ -13,6 +13,7 @@ n(n-1)/2 pairs, h.  The workload is n = 65536 values of the bimodal mixture
             inside the captured graph, against the FP32-issue / MUFU ALU bound.
   fp64      the all-binary64 GPU path on the same workload.
   batch     512 samples, n log-uniform in [256, 262144], in one batched call.
+  kde_eval  the density estimate of Eq. 1 for n = 2^20 values at 2^14 points.
   serving   the first requests of the seeded served stream (n log-uniform in
             [1000, 4194304], Poisson arrivals at 0.8 x the measured capacity)
             replayed through the continuous-batching server: p50/p99 latency.
@@ -58,6 +59,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="skip the 512-sample batch leg")
+    ap.add_argument("--no-eval", action="store_true", help="skip the density-estimate leg")
     ap.add_argument("--serve-requests", type=int, default=24,
                     help="requests of the served stream to replay (0: skip the serving leg)")
     ap.add_argument("--serve-load", type=float, default=0.8,
@@ -230,6 +232,37 @@ def batch_leg(kde, torch, dev, stream, flush, steps: int = 2, warmup: int = 1):
             "steps": steps, "input": "device-resident binary64, L2 flushed before each step"}
 
 
+def eval_leg(kde, torch, dev, stream, flush, steps: int = 3, warmup: int = 1):
+    """Density estimate (Eq. 1) of n = 2^20 normal values at m = 2^14 grid points with
+    the sample's own plug-in bandwidth, inputs resident on the device, FP32 path."""
+    import numpy as np
+
+    import synthdata
+    n, m = 1 << 20, 1 << 14
+    x = synthdata.normal(31, n) * 1.7 + 4.0
+    h = kde.kde_plugin_h(x, kde.KDE_FP32)["h"]
+    t = np.linspace(x.min(), x.max(), m)
+    xd = torch.tensor(x, dtype=torch.float64, device=dev)
+    td = torch.tensor(t, dtype=torch.float64, device=dev)
+    out = torch.empty(m, dtype=torch.float64, device=dev)
+    for _ in range(warmup):
+        kde.kde_eval(xd, h, td, kde.KDE_FP32, out=out, stream=stream)
+    ms = []
+    for _ in range(steps):
+        with torch.cuda.stream(stream):
+            flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        kde.kde_eval(xd, h, td, kde.KDE_FP32, out=out, stream=stream)
+        e1.record(stream)
+        stream.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    t_s = statistics.mean(ms) / 1e3
+    return {"n": n, "m": m, "h": h, "ms": 1e3 * t_s, "pair_evals_per_s": n * m / t_s,
+            "values": out.cpu().numpy(), "x": x, "t": t,
+            "includes": "copy of x and t into the workspace, sort of x, prescale, pairs, reduce"}
+
+
 def serve_leg(kde, capacity: float, count: int, load: float):
     """The first `count` requests of the served stream (n log-uniform in [1000, 4194304],
     FP32 samples, Poisson arrivals at `load` x the measured FP32 capacity), replayed in
@@ -382,7 +415,9 @@ def run_ours(args, ws, rank, local):
                 "pairs6_ms": statistics.mean(k6_64), "pairs4_ms": statistics.mean(k4_64),
                 "h": res64["h"]}
 
-    batch = serve = None
+    batch = serve = evl = None
+    if ws == 1 and not args.no_eval:
+        evl = eval_leg(kde, torch, dev, stream, flush)
     if ws == 1 and not args.no_batch:
         batch = batch_leg(kde, torch, dev, stream, flush)
     if ws == 1 and args.serve_requests > 0:
@@ -446,6 +481,16 @@ def run_ours(args, ws, rank, local):
             line["batch"]["fp32_batch_over_fp64_single"] = batch["pair_evals_per_s"] / fp64["value"]
     if serve:
         line["serving"] = serve
+    if evl:
+        # issue slots per pair: 3 FADD (double-float difference), FMUL, MUFU ex2,
+        # 0.75 FADD tree + 1 Kahan step per 4 terms; MUFU itself allows 32 per clock
+        slots = 6.75
+        eval_peak = sms * 2070e6 * min(128.0 / slots, rates_clk["mufu_ex2_per_clk_sm"])
+        line["kde_eval"] = {k: v for k, v in evl.items() if k not in ("values", "x", "t")}
+        line["kde_eval"]["roofline"] = {"bound": "alu", "achieved": evl["pair_evals_per_s"] / 1e9,
+                                        "peak": eval_peak / 1e9, "unit": "Gpair/s",
+                                        "frac": evl["pair_evals_per_s"] / eval_peak,
+                                        "peak_basis": f"{sms} SMs x 2070 MHz x 128 / {slots} slots per pair"}
     if not args.no_cpu_baseline:
         import oracle
         cores = oracle.default_threads()
@@ -457,6 +502,12 @@ def run_ours(args, ws, rank, local):
                                 "sample": f"one full PLUGIN run on the same n={n} sample "
                                           f"({pairs_per_step(n)} pair-evals, {dt:.2f} s)"}
         line["accuracy"]["rel_err_fp32_vs_oracle"] = rel_errors(res32, ref)
+        if evl:
+            import numpy as np
+            pick = np.linspace(0, evl["m"] - 1, 32).astype(int)
+            ref_e = oracle.kde_eval(evl["x"], evl["h"], evl["t"][pick], threads=cores)
+            line["kde_eval"]["max_rel_err_vs_oracle_32_points"] = float(
+                np.max(np.abs(evl["values"][pick] - ref_e) / ref_e))
         if fp64:
             line["accuracy"]["rel_err_fp64_vs_oracle"] = rel_errors(res64, ref)
     print(json.dumps(line))

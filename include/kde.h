@@ -148,6 +148,28 @@ KDE_API kde_status kde_plugin_h_batch(const double* x_packed, const int64_t* off
 KDE_API kde_status kde_psi_slots(const double* x, int64_t n, int r, double g, kde_precision prec,
                          double* slots, int64_t cap, int64_t* info);
 
+/* ---- density estimate -------------------------------------------------------- */
+
+/*
+ * kde_eval -- the kernel density estimate of Eq. 1 with the Gaussian kernel of
+ * Eq. 2 at m points: out[j] = (1 / (n h)) sum_i K((t[j] - x[i]) / h), usually
+ * with the h of kde_plugin_h.
+ *   x      n >= 1 binary64 sample values, host or device (read only).
+ *   t      m >= 1 binary64 evaluation points, host or device (read only).
+ *   h      bandwidth, finite and > 0.
+ *   prec   KDE_FP32: differences as double-float pairs, MUFU ex2, compensated
+ *          binary32 group sums folded into binary64 (every term is positive,
+ *          so nothing cancels); points farther than ~13.2 h from every sample
+ *          underflow to 0.  KDE_FP64: binary64 throughout.
+ *   out    m doubles, host or device.  Host: the call waits.  Device:
+ *          asynchronous on `stream`; invalid inputs then show as NaN in out.
+ * Errors: KDE_ERR_INVALID for null pointers, n < 1, m < 1, bad h or precision,
+ * a non-finite x or t, or (KDE_FP32) a value more than 1e7 bandwidths from the
+ * sample median.  Deterministic for given (n, m, device).
+ */
+KDE_API kde_status kde_eval(const double* x, int64_t n, double h, const double* t, int64_t m,
+                            kde_precision prec, double* out, void* stream);
+
 /* ---- tile-configuration autotuner -------------------------------------------- */
 
 /*

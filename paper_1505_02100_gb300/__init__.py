@@ -63,6 +63,7 @@ SIGNATURES = {
     "kde_plugin_h_batch": (_i32, [_vp, _vp, _i64, ctypes.c_int, _vp, _vp]),
     "kde_psi_slots": (_i32, [_vp, _i64, ctypes.c_int, _d, ctypes.c_int, _vp, _i64, _vp]),
     "kde_psi_static": (_i32, [_vp, _i64, ctypes.c_int, _d, ctypes.c_int, _vp, _vp]),
+    "kde_eval": (_i32, [_vp, _i64, _d, _vp, _i64, ctypes.c_int, _vp, _vp]),
     "kde_autotune": (_i32, [ctypes.c_int, _vp, ctypes.c_int]),
     "kde_autotune_clear": (_i32, [ctypes.c_int]),
     "kde_tile_config": (_i32, [ctypes.c_int, _i64, _vp]),
@@ -177,6 +178,20 @@ def kde_psi(x, r: int, g: float, prec: int = KDE_FP32, out=None, stream=None):
     st = load().kde_psi(p, n, int(r), float(g), int(prec), ctypes.addressof(v), _stream(stream))
     _check(st)
     return v.value
+
+
+def kde_eval(x, h: float, points, prec: int = KDE_FP32, out=None, stream=None):
+    """Eq. 1 with the Gaussian kernel (Eq. 2): fhat(t) = (1/(n h)) sum_i K((t - x_i)/h)
+    at every point.  Returns a numpy array, or None with a CUDA tensor `out` of
+    >= m float64 (asynchronous)."""
+    px, n, keep_x = _buf(x, np.float64)
+    pt, m, keep_t = _buf(points, np.float64)
+    if out is not None:
+        _check(load().kde_eval(px, n, float(h), pt, m, int(prec), out.data_ptr(), _stream(stream)))
+        return None
+    res = np.empty(m, dtype=np.float64)
+    _check(load().kde_eval(px, n, float(h), pt, m, int(prec), res.ctypes.data, _stream(stream)))
+    return res
 
 
 def kde_autotune(prec: int = KDE_FP32):

@@ -648,6 +648,7 @@ void kde_shutdown(void) {
     cudaSetDevice(prev);
   }
   R.ws.clear();
+  eval_release_all();
 }
 
 }  // extern "C"

@@ -157,6 +157,7 @@ int choose_config(int prec, int64_t n);    // tuner's force, environment, tuned 
 int default_config(int prec, int64_t n);   // the built-in rule
 SampleDesc make_desc(int prec, int cfg, int64_t n, double g_fixed);
 void drop_workspace(cudaStream_t stream);
+void eval_release_all();                     // kde_eval.cu: free the density-estimate workspaces
 
 // tile-configuration autotuner (kde_tune.cu)
 extern thread_local int t_tune_force_cfg;    // >= 0 only while the tuner times that configuration
