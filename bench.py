@@ -60,6 +60,8 @@ def parse():
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="skip the 512-sample batch leg")
     ap.add_argument("--no-eval", action="store_true", help="skip the density-estimate leg")
+    ap.add_argument("--no-tune", action="store_true",
+                    help="skip the tile autotuner (built-in rule or KDE_FP32_TILE_CONFIG)")
     ap.add_argument("--serve-requests", type=int, default=24,
                     help="requests of the served stream to replay (0: skip the serving leg)")
     ap.add_argument("--serve-load", type=float, default=0.8,
@@ -344,7 +346,7 @@ def run_ours(args, ws, rank, local):
         kbuild.build()
     barrier(ws)
     kde.load()
-    tuned = kde.kde_autotune(kde.KDE_FP32)     # tile configuration per size class, this device
+    tuned = None if args.no_tune else kde.kde_autotune(kde.KDE_FP32)   # per size class, this device
     n = args.n
     x = workload(n)
     xd = torch.tensor(x, dtype=torch.float64, device=dev)
