@@ -64,6 +64,13 @@ typedef enum {
                                 or the server is shutting down */
 } kde_status;
 
+/* KDE_FP32 holds each sample on a grid of step g 2^-F around its median, with
+ * F = 21 - floor(log2(R / g)) for R the smaller of twice the 0.1%-99.9%
+ * quantile radius and the largest deviation; pair differences on the grid are
+ * exact.  When the grid is coarse (F < 16) the rounding residual of each value
+ * is added to every difference as well.  Rounding only drops below the stated
+ * accuracy for extreme R / g (e.g. clusters thousands of bandwidths apart),
+ * where KDE_FP64 is the safer choice. */
 typedef enum {
     KDE_FP32 = 0,            /* binary32 pair terms, binary64 elsewhere */
     KDE_FP64 = 1             /* binary64 everywhere */
@@ -267,7 +274,10 @@ KDE_API kde_status kde_profile_enable(int on);
  * ms[1] pairs r = 6 (Steps IV-V; for kde_psi the one pairs launch); ms[2] the
  * second prescale; ms[3] pairs r = 4 (Steps VI-VII).  ms[2] and ms[3] are 0 for
  * kde_psi.  If cap >= 5, ms[4] is the number of kernel launches of that run
- * (the kernel nodes its CUDA graph replays).  cap >= 4.  KDE_ERR_INVALID if no
+ * (the kernel nodes its CUDA graph replays).  If cap >= 7, ms[5] and ms[6] are
+ * the unique pairs the r = 6 and r = 4 pair kernels skipped as far tile pairs
+ * (every term below 1e-31 in binary32, exactly 0 in binary64), summed over the
+ * run's samples; this waits for the run.  cap >= 4.  KDE_ERR_INVALID if no
  * profiled run happened there. */
 KDE_API kde_status kde_profile_last(void* stream, double* ms, int cap);
 

@@ -149,12 +149,14 @@ def kde_profile_enable(on: bool = True) -> None:
 
 def kde_profile_last(stream=None):
     """Device ms of the last profiled run on `stream`: setup (init + sort +
-    moments + prescale), pairs6, prescale4, pairs4; and `launches`, the number
-    of kernel launches of that run."""
-    ms = (ctypes.c_double * 5)()
-    _check(load().kde_profile_last(_stream(stream), ctypes.addressof(ms), 5))
+    moments + prescale), pairs6, prescale4, pairs4; `launches`, the number of
+    kernel launches of that run; `skipped6` / `skipped4`, the unique pairs the
+    pair kernels skipped as far tile pairs."""
+    ms = (ctypes.c_double * 7)()
+    _check(load().kde_profile_last(_stream(stream), ctypes.addressof(ms), 7))
     out = dict(zip(("setup", "pairs6", "prescale4", "pairs4"), list(ms)[:4]))
     out["launches"] = int(ms[4])
+    out["skipped6"], out["skipped4"] = int(ms[5]), int(ms[6])
     return out
 
 

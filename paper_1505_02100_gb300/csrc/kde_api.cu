@@ -233,6 +233,7 @@ struct Workspace {
   };
   std::unordered_map<uint64_t, GraphEntry> graphs;
   int last_launches = 0;   // kernel launches of the last run on this workspace
+  int64_t last_m = 0;      // samples of the last run on this workspace
   cudaEvent_t prof[5] = {};   // before init, after prescale r=6, after pairs r=6, after prescale r=4, after pairs r=4
   bool prof_valid = false;
 
@@ -457,6 +458,7 @@ kde_status run_plan(Workspace& W, const BatchPlan& P, const void* x, bool x_dev,
     for (cudaEvent_t& e : W.prof)
       if (!e) KDE_CU(cudaEventCreate(&e));
   }
+  W.last_m = static_cast<int64_t>(P.desc.size());
   if (!graphs_enabled()) return enqueue(W, P, s);
   const uint64_t gkey = P.key ^ (g_profile.load() ? 0x9E3779B97F4A7C15ull : 0ull);
   auto it = W.graphs.find(gkey);
@@ -616,7 +618,7 @@ kde_status kde_profile_enable(int on) {
 
 kde_status kde_profile_last(void* stream, double* ms, int cap) {
   if (!ms || cap < 4) return set_err(KDE_ERR_INVALID, "need room for 4 durations");
-  if (cap >= 5) ms[4] = 0.0;
+  for (int i = 4; i < cap && i < 7; ++i) ms[i] = 0.0;
   Workspace* W = nullptr;
   kde_status st = get_workspace(static_cast<cudaStream_t>(stream), &W);
   if (st != KDE_OK) return st;
@@ -629,6 +631,19 @@ kde_status kde_profile_last(void* stream, double* ms, int cap) {
     ms[i] = v;
   }
   if (cap >= 5) ms[4] = W->last_launches;
+  if (cap >= 7) {
+    // unique pairs the pair kernels skipped (far tile pairs), summed over the samples
+    std::vector<SampleState> h(static_cast<size_t>(W->last_m));
+    if (!h.empty())
+      KDE_CU(cudaMemcpy(h.data(), W->state.p, h.size() * sizeof(SampleState), cudaMemcpyDeviceToHost));
+    double s6 = 0.0, s4 = 0.0;
+    for (const SampleState& q : h) {
+      s6 += static_cast<double>(q.skipped[0]);
+      s4 += static_cast<double>(q.skipped[1]);
+    }
+    ms[5] = s6;
+    ms[6] = s4;
+  }
   return KDE_OK;
 }
 

@@ -36,7 +36,8 @@ constexpr int64_t kMomMaxBlocks = 256;
 constexpr int64_t kMaxChunks = int64_t(1) << 22;
 
 // Pair-kernel value representation.  The binary64 path holds u-units
-// z = (X - mean) / g.  The binary32 path holds y = M + round(z * 2^F) with
+// z = (X - median) / g.  The binary32 path holds a float2 (y, residual) with
+// residual = M + z 2^F - y and y = M + round(z * 2^F) with
 // M = 1.5 * 2^23: every value within 2^(22-F) bandwidths of the mean lies in
 // the binade [2^23, 2^24), so y_i - y_j is EXACT (Sterbenz) and only the
 // element-wise rounding (unbiased, first-order cancelling) remains.  The
@@ -82,6 +83,7 @@ struct SampleState {
   int32_t reserved;
   uint32_t done_mom;   // moments blocks finished (reset by the last one)
   uint32_t done_pairs; // chunks finished (reset by the last one)
+  unsigned long long skipped[2];   // unique pairs in far tile pairs not evaluated: psi6, psi4
 };
 
 struct MomentsArgs {

@@ -152,6 +152,7 @@ __global__ void init_states_kernel(const SampleDesc* desc, SampleState* state, i
   st->reserved = 0;
   st->done_mom = 0;
   st->done_pairs = 0;
+  st->skipped[0] = st->skipped[1] = 0;
 }
 
 // ---------------------------------------------------------------------------
@@ -293,17 +294,34 @@ __global__ void __launch_bounds__(kPrescaleThreads) prescale_kernel(PrescaleArgs
   const SampleState& st = a.state[k];
   if (st.res.status != KDE_OK) return;
   const double z = __dmul_rn(__dsub_rn(load_x(a.x, a.x_is_f32, d.x_off + i), st.center), st.scale);
-  if (d.prec == KDE_FP32) static_cast<float*>(a.y)[d.y_off + i] = static_cast<float>(kYBias + rint(z));
-  else static_cast<double*>(a.y)[d.y_off + i] = z;
+  if (d.prec == KDE_FP32) {
+    // grid value and what rounding to it left over: hi + lo = kYBias + z to ~2^-24
+    const float hi = static_cast<float>(kYBias + rint(z));
+    const float lo = static_cast<float>((kYBias + z) - static_cast<double>(hi));
+    static_cast<float2*>(a.y)[d.y_off + i] = make_float2(hi, lo);
+  } else {
+    static_cast<double*>(a.y)[d.y_off + i] = z;
+  }
 }
 
 // ---------------------------------------------------------------------------
 // Steps IV / VI: persistent triangular-tile pair kernel
 // ---------------------------------------------------------------------------
 
+// T: the arithmetic type of the pair terms; Y: the stored scaled value
+// (binary32: grid value and rounding residual; binary64: u-units).
 template <int PREC> struct Arith;
-template <> struct Arith<KDE_FP32> { using T = float; };
-template <> struct Arith<KDE_FP64> { using T = double; };
+template <> struct Arith<KDE_FP32> { using T = float; using Y = float2; };
+template <> struct Arith<KDE_FP64> { using T = double; using Y = double; };
+__device__ __forceinline__ float hi_of(float2 v) { return v.x; }
+__device__ __forceinline__ float lo_of(float2 v) { return v.y; }
+__device__ __forceinline__ double hi_of(double v) { return v; }
+__device__ __forceinline__ float lo_of(double) { return 0.0f; }
+
+// Below this grid exponent the binary32 path adds the rounding residuals to
+// each difference (two more FADDs per pair): rounding to a grid of step
+// g 2^-F would otherwise perturb psi_r by up to ~1e-5 (measured at F = 13).
+constexpr int kFLo = 16;
 
 // Hermite factor of K^(r) on v = u^2, u = (X_i - X_j)/g, with the integer
 // coefficients printed in Steps IV and VI (exact in binary32):
@@ -377,13 +395,12 @@ __device__ __forceinline__ float exp2_reduced(float f) {
   return __fmaf_rn(q, f, 1.0f);
 }
 
-// One pair term, binary32, without its 2^(-v c_lo) factor: a, b scaled values
-// (grid units); c_hi = 2^(-2F) / (2 ln 2) rounded; vmax = kMinT / c_hi.
+// One pair term, binary32, without its 2^(-v c_lo) factor: d = y_i - y_j in grid
+// units; c_hi = 2^(-2F) / (2 ln 2) rounded; vmax = kMinT / c_hi.
 // `vout` receives v: the term is too large by the relative amount v c_lo ln 2.
 template <int RORD, bool CLAMP>
-__device__ __forceinline__ float term32(float a, float b, const Coef<float, RORD>& cf, float c_hi,
-                                        float vmax, float& vout) {
-  const float d = __fsub_rn(a, b);                        // exact (see kde_internal.cuh)
+__device__ __forceinline__ float term32(float d, const Coef<float, RORD>& cf, float c_hi, float vmax,
+                                        float& vout) {
   const float v = CLAMP ? fminf(__fmul_rn(d, d), vmax) : __fmul_rn(d, d);
   const float yb = __fmaf_rn(v, -c_hi, kRoundMagic);      // low bits: k = round(t)
   const float kf = __fsub_rn(yb, kRoundMagic);
@@ -429,8 +446,9 @@ struct Kahan32 {
 // summation of such runs drifts systematically, which the cancellation of the
 // pair sum would amplify.  Per row, sum(term * v) feeds the c_lo correction
 // (see term32), which goes to the thread's binary64 total `cacc`.
-template <int RORD, int ROWS, int CJ, int TILE, bool CLAMP>
-__device__ __forceinline__ void tile_pass(const float* __restrict__ tile, const float (&w)[ROWS],
+template <int RORD, int ROWS, int CJ, int TILE, bool CLAMP, bool LO>
+__device__ __forceinline__ void tile_pass(const float* __restrict__ tile, const float* __restrict__ tile_lo,
+                                          const float (&w)[ROWS], const float (&wl)[ROWS],
                                           const Coef<float, RORD>& cf, float c_hi, double c_lo_ln2,
                                           float vmax, Kahan32& acc, double& cacc) {
   static_assert(CJ == 4, "one float4 of columns per group of terms");
@@ -439,11 +457,15 @@ __device__ __forceinline__ void tile_pass(const float* __restrict__ tile, const 
   for (int r = 0; r < ROWS; ++r) sum[r] = comp[r] = tv[r] = 0.0f;
 #pragma unroll 1
   for (int jj = 0; jj < TILE; jj += CJ) {
-    float b[CJ];
+    float b[CJ], bl[CJ];
 #pragma unroll
     for (int q4 = 0; q4 < CJ; q4 += 4) {
       const float4 v4 = *reinterpret_cast<const float4*>(tile + jj + q4);
       b[q4] = v4.x; b[q4 + 1] = v4.y; b[q4 + 2] = v4.z; b[q4 + 3] = v4.w;
+      if (LO) {
+        const float4 l4 = *reinterpret_cast<const float4*>(tile_lo + jj + q4);
+        bl[q4] = l4.x; bl[q4 + 1] = l4.y; bl[q4 + 2] = l4.z; bl[q4 + 3] = l4.w;
+      }
     }
 #pragma unroll
     for (int r = 0; r < ROWS; ++r) {
@@ -451,7 +473,9 @@ __device__ __forceinline__ void tile_pass(const float* __restrict__ tile, const 
 #pragma unroll
       for (int q = 0; q < CJ; ++q) {
         float v;
-        t[q] = term32<RORD, CLAMP>(w[r], b[q], cf, c_hi, vmax, v);
+        // grid difference (exact), plus the residuals when the grid is coarse
+        const float d = LO ? __fadd_rn(__fsub_rn(w[r], b[q]), __fsub_rn(wl[r], bl[q])) : __fsub_rn(w[r], b[q]);
+        t[q] = term32<RORD, CLAMP>(d, cf, c_hi, vmax, v);
         tv[r] = __fmaf_rn(t[q], v, tv[r]);
       }
       const float g4 = __fadd_rn(__fadd_rn(t[0], t[1]), __fadd_rn(t[2], t[3]));
@@ -542,12 +566,22 @@ __device__ void finalize_pairs(const PairArgs& a, const SampleDesc& d, SampleSta
   }
 }
 
+// Register budget per thread: binary32 64 with 4 rows (the fast path needs no
+// more), 96 with 8; binary64 128 (its inlined exp would otherwise take ~170).
+template <int PREC, int THREADS, int ROWS>
+constexpr int pair_min_blocks() {
+  return 65536 / ((PREC != KDE_FP32 ? 128 : ROWS >= 8 ? 96 : 64) * THREADS) > 0
+             ? 65536 / ((PREC != KDE_FP32 ? 128 : ROWS >= 8 ? 96 : 64) * THREADS)
+             : 1;
+}
+
 template <int PREC, int THREADS, int ROWS, int CJ, int RORD>
-__global__ void __launch_bounds__(THREADS) pairs_kernel(PairArgs a) {
+__global__ void __launch_bounds__(THREADS, (pair_min_blocks<PREC, THREADS, ROWS>())) pairs_kernel(PairArgs a) {
   using T = typename Arith<PREC>::T;
   constexpr int TILE = THREADS * ROWS;
   static_assert(TILE % 8 == 0, "tile");
   __shared__ __align__(16) T tile[TILE];
+  __shared__ __align__(16) float tile_lo[PREC == KDE_FP32 ? TILE : 4];
   __shared__ double red[THREADS / 32 + 1];
   __shared__ long long s_item;
   __shared__ int s_last;
@@ -567,7 +601,8 @@ __global__ void __launch_bounds__(THREADS) pairs_kernel(PairArgs a) {
     double part = 0.0;
     double diag_units = 0.0;
     if (st->res.status == KDE_OK) {
-      const T* __restrict__ y = static_cast<const T*>(a.y) + d.y_off;
+      using Y = typename Arith<PREC>::Y;
+      const Y* __restrict__ y = static_cast<const Y*>(a.y) + d.y_off;
       const T pad_lo = static_cast<T>(st->pad_lo), pad_hi = static_cast<T>(st->pad_hi);
       const double p2 = ldexp(1.0, -2 * st->F);
       const float c_hi = static_cast<float>(kInvTwoLn2 * p2);
@@ -581,24 +616,57 @@ __global__ void __launch_bounds__(THREADS) pairs_kernel(PairArgs a) {
       int64_t I, J;
       tri_index(p, d.nt, I, J);
       T w[ROWS];
+      float wl[ROWS];
       // row slot r of this thread holds sample I*TILE + tid*ROWS + r
       auto load_rows = [&](int64_t I_) {
 #pragma unroll
         for (int r = 0; r < ROWS; ++r) {
           const int64_t i = I_ * TILE + static_cast<int64_t>(tid) * ROWS + r;
-          w[r] = i < d.n ? y[i] : pad_lo;
+          if (i < d.n) {
+            const Y v = y[i];
+            w[r] = hi_of(v);
+            wl[r] = lo_of(v);
+          } else {
+            w[r] = pad_lo;
+            wl[r] = 0.0f;
+          }
         }
       };
+      const bool lo_path = PREC == KDE_FP32 && st->F < kFLo;
+      const double margin = PREC == KDE_FP32 ? 1.0 : 0.0;   // |residual differences| <= 1 grid unit
       load_rows(I);
       Kahan32 acc32;
       double cacc = 0.0;
       double acc64 = 0.0;
+      // Far tile pairs are skipped: the sample is sorted, so the smallest distance
+      // of an off-diagonal tile pair is its first column minus its last row.  Beyond
+      // the binary32 clamp every term is below 1e-31; beyond 40 bandwidths every
+      // binary64 term underflows to exactly 0.
+      const double far2 = (PREC == KDE_FP32) ? static_cast<double>(vmax) : 1600.0;
+      int64_t skipped_pairs = 0;
       for (; p < pend; ++p) {
+        bool far = false;
+        if (J > I) {
+          const double gap = static_cast<double>(hi_of(y[J * TILE])) -
+                             static_cast<double>(hi_of(y[I * TILE + TILE - 1])) - margin;
+          far = gap > 0.0 && gap * gap > far2;
+        }
+        if (far) {
+          const int64_t cols = d.n - J * TILE;
+          skipped_pairs += static_cast<int64_t>(TILE) * (cols < TILE ? cols : TILE);
+        } else {
         __syncthreads();
 #pragma unroll
         for (int r = 0; r < ROWS; ++r) {
           const int64_t j = J * TILE + tid + r * THREADS;
-          tile[tid + r * THREADS] = j < d.n ? y[j] : pad_hi;
+          if (j < d.n) {
+            const Y v = y[j];
+            tile[tid + r * THREADS] = hi_of(v);
+            if (PREC == KDE_FP32) tile_lo[tid + r * THREADS] = lo_of(v);
+          } else {
+            tile[tid + r * THREADS] = pad_hi;
+            if (PREC == KDE_FP32) tile_lo[tid + r * THREADS] = 0.0f;
+          }
         }
         __syncthreads();
         // A diagonal tile pair (I == J) is evaluated in full with halved
@@ -609,16 +677,22 @@ __global__ void __launch_bounds__(THREADS) pairs_kernel(PairArgs a) {
         if constexpr (PREC == KDE_FP32) {
           // The sample is sorted, so the largest |y_i - y_j| of the tile pair is
           // its last column minus its first row; tiles with padding always clamp.
-          const double span = static_cast<double>(tile[TILE - 1]) - static_cast<double>(y[I * TILE]);
+          const double span = static_cast<double>(tile[TILE - 1]) - static_cast<double>(hi_of(y[I * TILE])) + margin;
           const bool near = (J + 1) * TILE <= d.n && span * span <= static_cast<double>(vmax);
-          if (near) tile_pass<RORD, ROWS, CJ, TILE, false>(tile, w, cf, c_hi, c_lo_ln2, vmax, acc32, cacc);
-          else tile_pass<RORD, ROWS, CJ, TILE, true>(tile, w, cf, c_hi, c_lo_ln2, vmax, acc32, cacc);
+          if (lo_path) {
+            if (near) tile_pass<RORD, ROWS, CJ, TILE, false, true>(tile, tile_lo, w, wl, cf, c_hi, c_lo_ln2, vmax, acc32, cacc);
+            else tile_pass<RORD, ROWS, CJ, TILE, true, true>(tile, tile_lo, w, wl, cf, c_hi, c_lo_ln2, vmax, acc32, cacc);
+          } else {
+            if (near) tile_pass<RORD, ROWS, CJ, TILE, false, false>(tile, tile_lo, w, wl, cf, c_hi, c_lo_ln2, vmax, acc32, cacc);
+            else tile_pass<RORD, ROWS, CJ, TILE, true, false>(tile, tile_lo, w, wl, cf, c_hi, c_lo_ln2, vmax, acc32, cacc);
+          }
         } else {
           tile_pass64<RORD, ROWS, TILE>(tile, w, cf, acc64);
         }
         if (diag) {
           const int64_t valid = d.n - I * TILE;
           diag_units += static_cast<double>(valid < TILE ? valid : TILE);
+        }
         }
         if (++J == d.nt) {
           ++I;
@@ -627,6 +701,8 @@ __global__ void __launch_bounds__(THREADS) pairs_kernel(PairArgs a) {
         }
       }
       part = (PREC == KDE_FP32) ? acc32.value() + cacc : acc64;
+      if (tid == 0 && skipped_pairs > 0)
+        atomicAdd(&st->skipped[RORD == 6 ? 0 : 1], static_cast<unsigned long long>(skipped_pairs));
     }
     const double tot = block_sum<THREADS>(part, red);
     if (tid == 0) {

@@ -205,7 +205,7 @@ struct ServerImpl {
     r.cfg = choose_config(r.prec, r.n);
     r.d = make_desc(r.prec, r.cfg, r.n, 0.0);
     r.b_x = sizeof(float) * static_cast<size_t>(r.n);
-    r.b_y = (r.prec == KDE_FP32 ? sizeof(float) : sizeof(double)) * static_cast<size_t>(r.n);
+    r.b_y = sizeof(double) * static_cast<size_t>(r.n);   // float2 (binary32) or double (binary64)
     r.b_s = sizeof(double) * static_cast<size_t>(r.d.nchunks);
     r.b_m = sizeof(double) * 5 * static_cast<size_t>(r.d.mblocks);
     r.cost_per_pair = r.prec == KDE_FP64 ? kFp64Cost : 1.0;
@@ -228,7 +228,7 @@ struct ServerImpl {
       r->slot = free_slots.back();
       free_slots.pop_back();
       r->d.x_off = static_cast<int64_t>(r->off_x / sizeof(float));
-      r->d.y_off = static_cast<int64_t>(r->off_y / (r->prec == KDE_FP32 ? sizeof(float) : sizeof(double)));
+      r->d.y_off = static_cast<int64_t>(r->off_y / 8);   // float2 or double elements
       r->d.tmp_off = static_cast<int64_t>(r->off_y / sizeof(float));   // sort scratch: the y region
       r->d.slot_off = static_cast<int64_t>(r->off_s / sizeof(double));
       r->d.mslot_off = static_cast<int64_t>(r->off_m / sizeof(double));

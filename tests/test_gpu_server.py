@@ -65,7 +65,7 @@ def test_server_admission_errors_and_timeout(kde):
         with pytest.raises(kde.KdeError) as e:
             srv.submit(np.zeros(1, dtype=np.float32))
         assert e.value.status == kde.KDE_ERR_INVALID
-        t = srv.submit(synthdata.normal(5, 300000).astype(np.float32))
+        t = srv.submit(synthdata.normal(5, 150000).astype(np.float32))   # ~2.6 MB footprint
         r = srv.poll(t, timeout_ms=0)
         assert r is None or r[0]["status"] == 0
         assert srv.poll(t, timeout_ms=60000) is not None or True

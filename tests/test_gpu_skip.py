@@ -1,0 +1,72 @@
+"""Far tile pairs: skipped by the pair kernels, counted, and the results still match
+the oracle (binary64 terms there are exactly 0; binary32 ones are below 1e-31)."""
+import numpy as np
+import pytest
+
+import oracle
+import synthdata
+
+pytestmark = pytest.mark.gpu
+
+TOL = {0: 1e-5, 1: 1e-11}
+
+
+@pytest.fixture(scope="module")
+def kde():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1505_02100_gb300 as k
+    return k
+
+
+def _rel(a, b):
+    return abs(a - b) / abs(b)
+
+
+@pytest.mark.parametrize("r,g", [(6, 0.3), (4, 0.2)])
+def test_two_far_clusters(kde, r, g):
+    import torch
+    # 60 sigma apart: every cross-cluster tile pair is beyond 13 bandwidths, while the
+    # sample's range stays ~200 bandwidths (the binary32 grid keeps F >= 14)
+    a = synthdata.normal(90, 30000)
+    b = synthdata.normal(91, 30000) + 60.0
+    x = np.concatenate([a, b])
+    ref = oracle.psi(x, r, g)
+    cross = a.size * b.size
+    for prec in (0, 1):
+        s = torch.cuda.Stream()
+        kde.kde_profile_enable(True)
+        try:
+            got = kde.kde_psi(x, r, g, prec, stream=s)
+            t = kde.kde_profile_last(s)
+        finally:
+            kde.kde_profile_enable(False)
+        assert _rel(got, ref) <= TOL[prec], (prec, got, ref)
+        skipped = t["skipped6"] if r == 6 else t["skipped4"]
+        # every cross-cluster pair but those in the one or two straddling tiles,
+        # plus far pairs inside each cluster's tails
+        assert 0.95 * cross <= skipped <= x.size * (x.size - 1) // 2, (prec, skipped, cross)
+
+
+def test_heavy_tails_plugin_parity(kde):
+    x = synthdata.student_t3(92, 200000) * 3.0
+    ref = oracle.plugin(x)
+    for prec in (0, 1):
+        got = kde.kde_plugin_h(x, prec)
+        assert got["status"] == 0
+        for f in ("psi6", "psi4", "h"):
+            assert _rel(got[f], ref[f]) <= TOL[prec], (prec, f)
+
+
+def test_fp32_coarse_grid_with_residuals(kde):
+    """Far-apart clusters with a tiny g push the binary32 grid exponent down to
+    F = 10 (R / g ~ 3300); the rounding residuals keep the stated accuracy."""
+    a = synthdata.normal(93, 30000)
+    b = synthdata.normal(94, 30000) + 1000.0
+    x = np.concatenate([a, b])
+    ref = oracle.psi(x, 6, 0.3)
+    assert _rel(kde.kde_psi(x, 6, 0.3, 1), ref) <= TOL[1]
+    assert _rel(kde.kde_psi(x, 6, 0.3, 0), ref) <= TOL[0]
