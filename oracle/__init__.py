@@ -35,6 +35,18 @@ class Result(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class StageResult(ctypes.Structure):
+    _fields_ = [("mean", ctypes.c_double), ("sigma", ctypes.c_double),
+                ("psi", ctypes.c_double * 6), ("g", ctypes.c_double * 6), ("h", ctypes.c_double),
+                ("stages", ctypes.c_int), ("status", ctypes.c_int)]
+
+    def as_dict(self):
+        return {"mean": self.mean, "sigma": self.sigma, "h": self.h, "stages": self.stages,
+                "status": self.status,
+                "psi": {2 * k + 4: self.psi[k] for k in range(6)},
+                "g": {2 * k + 4: self.g[k] for k in range(6)}}
+
+
 class ResultLD(ctypes.Structure):
     _fields_ = [(k, ctypes.c_longdouble) for k in
                 ("mean", "sigma", "psi8", "g1", "psi6", "g2", "psi4", "h")] + [("status", ctypes.c_int)]
@@ -76,6 +88,7 @@ def _load():
                                       ctypes.POINTER(ctypes.c_longdouble)]
         lib.oracle_long_double_mantissa_bits.restype = ip
         lib.oracle_kde_eval.argtypes = [dp, i64, d, dp, i64, ip, dp]
+        lib.oracle_plugin_stages.argtypes = [dp, i64, ip, ip, ip, ctypes.POINTER(StageResult)]
         _lib = lib
     return _lib
 
@@ -106,7 +119,7 @@ def moments(x):
 
 
 def kernel_deriv(r: int, u: float) -> float:
-    """K^(r)(u), r in {4, 6} (Algorithm 1, Steps IV and VI)."""
+    """K^(r)(u), r in {4, 6} (Algorithm 1, Steps IV and VI) and r in {8, 10}."""
     return _load().oracle_kernel_deriv(int(r), float(u))
 
 
@@ -172,3 +185,13 @@ def kde_eval(x, h: float, points, threads: int | None = None) -> np.ndarray:
     if st != OK:
         raise ValueError(f"oracle_kde_eval status {st}")
     return out
+
+
+def plugin_stages(x, stages: int, form: int = FORM_SYMMETRIC, threads: int | None = None) -> dict:
+    """The l-stage direct plug-in (l = stages, 1..4): psi_{2l+4} by the normal scale,
+    then psi_{2l+2} .. psi_4 at pilot bandwidths, then h; l = 2 is Algorithm 1."""
+    a = _arr(x)
+    res = StageResult()
+    _load().oracle_plugin_stages(_ptr(a), a.size, int(stages), int(form),
+                                 int(threads or default_threads()), ctypes.byref(res))
+    return res.as_dict()

@@ -65,20 +65,23 @@ int oracle_moments(const double* x, int64_t n, double* mean, double* var) {
 
 /* ---- kernel derivatives, Steps IV and VI ------------------------------------ */
 /* K^(6)(x) = (x^6 - 15 x^4 + 45 x^2 - 15) exp(-x^2/2) / sqrt(2 pi)
- * K^(4)(x) = (x^4 - 6 x^2 + 3) exp(-x^2/2) / sqrt(2 pi)                        */
+ * K^(4)(x) = (x^4 - 6 x^2 + 3) exp(-x^2/2) / sqrt(2 pi)
+ * and, for the stages above Algorithm 1's two, the same Hermite form:
+ * K^(8)(x)  = (x^8 - 28 x^6 + 210 x^4 - 420 x^2 + 105) exp(-x^2/2) / sqrt(2 pi)
+ * K^(10)(x) = (x^10 - 45 x^8 + 630 x^6 - 3150 x^4 + 4725 x^2 - 945) exp(-x^2/2) / sqrt(2 pi) */
 double oracle_kernel_deriv(int r, double x) {
     double x2 = x * x;
     double e = exp(-0.5 * x2);
-    if (r == 6) {
-        double x4 = x2 * x2, x6 = x4 * x2;
-        return inv_sqrt_2pi() * (x6 - 15.0 * x4 + 45.0 * x2 - 15.0) * e;
-    }
-    if (r == 4) {
-        double x4 = x2 * x2;
-        return inv_sqrt_2pi() * (x4 - 6.0 * x2 + 3.0) * e;
-    }
+    double x4 = x2 * x2, x6 = x4 * x2, x8 = x4 * x4;
+    if (r == 6) return inv_sqrt_2pi() * (x6 - 15.0 * x4 + 45.0 * x2 - 15.0) * e;
+    if (r == 4) return inv_sqrt_2pi() * (x4 - 6.0 * x2 + 3.0) * e;
+    if (r == 8) return inv_sqrt_2pi() * (x8 - 28.0 * x6 + 210.0 * x4 - 420.0 * x2 + 105.0) * e;
+    if (r == 10)
+        return inv_sqrt_2pi() * (x8 * x2 - 45.0 * x8 + 630.0 * x6 - 3150.0 * x4 + 4725.0 * x2 - 945.0) * e;
     return NAN;
 }
+
+static int valid_order(int r) { return r == 4 || r == 6 || r == 8 || r == 10; }
 
 /* ---- the O(n^2) functional ---------------------------------------------------- */
 typedef struct {
@@ -117,7 +120,7 @@ static void* psi_worker(void* arg) {
 
 int oracle_psi(const double* x, int64_t n, int r, double g, int form, int nthreads,
                double* psi) {
-    if (!x || !psi || n < 1 || (r != 4 && r != 6) || !(g > 0) || !isfinite(g))
+    if (!x || !psi || n < 1 || !valid_order(r) || !(g > 0) || !isfinite(g))
         return ORACLE_ERR_INVALID;
     if (form != ORACLE_FORM_FULL && form != ORACLE_FORM_SYMMETRIC) return ORACLE_ERR_INVALID;
     psi_job jb = {x, n, r, g, form, (double*)malloc(sizeof(double) * (size_t)n), 0};
@@ -147,7 +150,7 @@ int oracle_psi(const double* x, int64_t n, int r, double g, int form, int nthrea
 
 int oracle_psi_block(const double* x, int64_t n, int64_t i0, int64_t i1, int64_t j0,
                      int64_t j1, int r, double g, double* sum, double* abs_sum) {
-    if (!x || !sum || !abs_sum || (r != 4 && r != 6) || !(g > 0)) return ORACLE_ERR_INVALID;
+    if (!x || !sum || !abs_sum || !valid_order(r) || !(g > 0)) return ORACLE_ERR_INVALID;
     if (i0 < 0 || j0 < 0 || i1 > n || j1 > n) return ORACLE_ERR_INVALID;
     csum s = {0, 0}, a = {0, 0};
     for (int64_t i = i0; i < i1; ++i) {
@@ -200,6 +203,57 @@ int oracle_plugin(const double* x, int64_t n, int form, int nthreads, oracle_res
     if (!(out->psi4 > 0)) { out->status = ORACLE_ERR_DOMAIN; return out->status; }
     /* Step VII */
     out->h = pow(RK / (mu2 * mu2 * out->psi4 * nn), 1.0 / 5.0);
+    out->status = ORACLE_OK;
+    return ORACLE_OK;
+}
+
+/* ---- the l-stage direct plug-in: Algorithm 1 with l estimated functionals --------- */
+/* Stage count l: psi_{2l+4} by the normal scale (Step II's formula, general r:
+ * (-1)^(r/2) r! / ((2 sigma)^(r+1) (r/2)! sqrt(pi))), then for r = 2l+2, ..., 4
+ * the pilot g_r = (-2 K^(r)(0) / (mu2 psi_{r+2} n))^(1/(r+3)) (Steps III and V)
+ * and psi_r(g_r) (Steps IV and VI), then h (Step VII).  l = 2 is Algorithm 1. */
+static double kernel_deriv_at_zero(int r) {          /* K^(r)(0) = He_r(0) / sqrt(2 pi) */
+    double he = 1.0;                                  /* He_r(0) = (-1)^(r/2) (r-1)!! */
+    for (int k = r - 1; k > 1; k -= 2) he *= (double)k;
+    return ((r / 2) % 2 ? -he : he) * inv_sqrt_2pi();
+}
+
+static double normal_scale_psi(int r, double sigma) {
+    double num = 1.0, den = 1.0;                      /* r! and (r/2)! */
+    for (int k = 2; k <= r; ++k) num *= (double)k;
+    for (int k = 2; k <= r / 2; ++k) den *= (double)k;
+    double v = num / (pow(2.0 * sigma, (double)(r + 1)) * den * sqrt(PI));
+    return (r / 2) % 2 ? -v : v;
+}
+
+int oracle_plugin_stages(const double* x, int64_t n, int stages, int form, int nthreads,
+                         oracle_stage_result* out) {
+    if (!out) return ORACLE_ERR_INVALID;
+    out->mean = out->sigma = out->h = NAN;
+    for (int k = 0; k < 6; ++k) out->psi[k] = out->g[k] = NAN;
+    out->stages = stages;
+    out->status = ORACLE_ERR_INVALID;
+    if (!x || n < 2 || stages < 1 || stages > 4) return out->status;
+    double nn = (double)n, mean, var;
+    int st = oracle_moments(x, n, &mean, &var);                 /* Step I */
+    if (st != ORACLE_OK) { out->status = st; return st; }
+    out->mean = mean;
+    out->sigma = sqrt(var);
+    if (!(out->sigma > 0)) { out->status = ORACLE_ERR_DEGENERATE; return out->status; }
+    int top = 2 * stages + 4;
+    double psi_up = normal_scale_psi(top, out->sigma);          /* Step II */
+    out->psi[top / 2 - 2] = psi_up;
+    for (int r = top - 2; r >= 4; r -= 2) {
+        double ratio = -2.0 * kernel_deriv_at_zero(r) / (psi_up * nn);   /* mu2 = 1 */
+        if (!(ratio > 0)) { out->status = ORACLE_ERR_DOMAIN; return out->status; }
+        double g = pow(ratio, 1.0 / (double)(r + 3));             /* Steps III, V */
+        out->g[r / 2 - 2] = g;
+        st = oracle_psi(x, n, r, g, form, nthreads, &psi_up);      /* Steps IV, VI */
+        if (st != ORACLE_OK) { out->status = st; return st; }
+        out->psi[r / 2 - 2] = psi_up;
+    }
+    if (!(psi_up > 0)) { out->status = ORACLE_ERR_DOMAIN; return out->status; }
+    out->h = pow(1.0 / (2.0 * sqrt(PI)) / (psi_up * nn), 1.0 / 5.0);   /* Step VII */
     out->status = ORACLE_OK;
     return ORACLE_OK;
 }

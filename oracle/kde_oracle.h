@@ -43,10 +43,22 @@ typedef struct {
     int status;
 } oracle_result_ld;
 
+/* l-stage plug-in: psi[k] and g[k] belong to r = 2k + 4 (psi_4 .. psi_14);
+ * the top one is the normal-scale functional (its g is NaN), unused ones NaN. */
+typedef struct {
+    double mean, sigma;
+    double psi[6];
+    double g[6];
+    double h;
+    int stages;
+    int status;
+} oracle_stage_result;
+
 /* Step I: mean and unbiased variance (divisor n-1), two-pass. */
 int oracle_moments(const double* x, int64_t n, double* mean, double* var);
 
-/* K^(r)(u) for r in {4, 6}, the printed Hermite forms of Steps IV and VI. */
+/* K^(r)(u) for r in {4, 6} (the printed Hermite forms of Steps IV and VI) and
+ * r in {8, 10} (the same form, for the stages above Algorithm 1's two). */
 double oracle_kernel_deriv(int r, double u);
 
 /* psi_r(g) = n^-2 g^-(r+1) sum_i sum_j K^(r)((X_i - X_j)/g), Steps IV / VI. */
@@ -60,6 +72,13 @@ int oracle_psi_block(const double* x, int64_t n, int64_t i0, int64_t i1, int64_t
 
 /* The whole of Algorithm 1, Steps I-VII. */
 int oracle_plugin(const double* x, int64_t n, int form, int nthreads, oracle_result* out);
+
+/* The l-stage direct plug-in, l = stages in 1..4: psi_{2l+4} by the normal
+ * scale, then psi_{2l+2}, ..., psi_4 each at the pilot bandwidth computed from
+ * the one above it (the form of Steps III and V), then h (Step VII).  l = 2 is
+ * Algorithm 1.  K^(r) for r in {4, 6, 8, 10}. */
+int oracle_plugin_stages(const double* x, int64_t n, int stages, int form, int nthreads,
+                         oracle_stage_result* out);
 
 /* Brute force in long double: full double loop, plain summation. */
 int oracle_plugin_ld(const double* x, int64_t n, oracle_result_ld* out);

@@ -32,7 +32,7 @@ def _mp_phi(u):
 # Kernel derivatives K^(r) (Algorithm 1, Steps IV and VI)
 # --------------------------------------------------------------------------
 
-@pytest.mark.parametrize("r", [4, 6])
+@pytest.mark.parametrize("r", [4, 6, 8, 10])
 @pytest.mark.parametrize("u", [0.0, 0.3, -1.0, 1.7, 2.5, -4.0, 6.25, 9.0])
 def test_kernel_deriv_is_rth_derivative_of_gaussian(r, u):
     """K^(r)(u) equals d^r/du^r of the Gaussian kernel, taken numerically (no Hermite form)."""
@@ -60,7 +60,7 @@ def test_printed_polynomials_are_hermite_derivatives():
             assert p == pytest.approx(float(mp.diff(_mp_phi, mp.mpf(u), r)), rel=1e-13, abs=1e-16)
 
 
-@pytest.mark.parametrize("r", [4, 6])
+@pytest.mark.parametrize("r", [4, 6, 8, 10])
 def test_kernel_deriv_moment_identities(r):
     """Integration by parts: int K^(r) = 0 and int u^r K^(r)(u) du = r! for even r."""
     from scipy.integrate import quad
@@ -93,7 +93,7 @@ def _psi_by_derivative(x, r, g):
 
 
 @pytest.mark.parametrize("form", [oracle.FORM_FULL, oracle.FORM_SYMMETRIC])
-@pytest.mark.parametrize("r", [4, 6])
+@pytest.mark.parametrize("r", [4, 6, 8, 10])
 @pytest.mark.parametrize("case", ["two", "three", "toy8"])
 def test_psi_equals_rth_derivative_of_pair_density(form, r, case, toy8):
     x = {"two": [0.0, 1.0], "three": [0.0, 1.0, 3.0], "toy8": list(toy8)}[case]
@@ -102,7 +102,7 @@ def test_psi_equals_rth_derivative_of_pair_density(form, r, case, toy8):
         assert oracle.psi(x, r, g, form=form, threads=1) == pytest.approx(ref, rel=1e-13)
 
 
-@pytest.mark.parametrize("r", [4, 6])
+@pytest.mark.parametrize("r", [4, 6, 8, 10])
 def test_psi_is_integral_of_squared_kde_derivative(r, toy8):
     """Convolution identity: psi_r(sqrt(2) b) = (-1)^(r/2) int (f_b^(r/2)(x))^2 dx,
     f_b the Gaussian KDE of the data with bandwidth b (Eq. 1)."""
@@ -124,7 +124,7 @@ def test_psi_is_integral_of_squared_kde_derivative(r, toy8):
     assert oracle.psi(x, r, math.sqrt(2) * b, threads=1) == pytest.approx(ref, rel=1e-9)
 
 
-@pytest.mark.parametrize("r", [4, 6])
+@pytest.mark.parametrize("r", [4, 6, 8, 10])
 def test_full_and_symmetric_forms_agree(r):
     """Step IV/VI printed double sum vs Eqs. (6)-(7) (2 * sum_{i<j} + n K^(r)(0))."""
     x = synthdata.normal(11, 700) * 1.7 + 0.3
