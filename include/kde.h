@@ -52,7 +52,7 @@ extern "C" {
 
 typedef enum {
     KDE_OK = 0,
-    KDE_ERR_INVALID = 1,     /* null pointer, n < 2, r not in {4,6}, g <= 0 or not finite,
+    KDE_ERR_INVALID = 1,     /* null pointer, n < 2, r not in {4,6,8,10}, g <= 0 or not finite,
                                 non-finite data, or data whose range overflows the format */
     KDE_ERR_DEGENERATE = 2,  /* sample standard deviation is zero (Step I) */
     KDE_ERR_DOMAIN = 3,      /* psi6 >= 0 (g2 undefined, Step V) or psi4 <= 0 (h undefined,
@@ -91,11 +91,25 @@ typedef struct {
     int32_t reserved;
 } kde_result;
 
+/* Results of the l-stage plug-in (kde_plugin_h_stages).  psi[k] and g[k]
+ * belong to the order r = 2k + 4 (psi_4, psi_6, ..., psi_14): g[k] is the pilot
+ * bandwidth psi_r was estimated at; the top order 2l + 4 holds the normal-scale
+ * value (its g is NaN); unused entries are NaN. */
+typedef struct {
+    double mean, sigma;
+    double psi[6];
+    double g[6];
+    double h;
+    int32_t stages;
+    int32_t status;
+} kde_stage_result;
+
 /*
  * kde_psi -- the functional psi_r(g) of Steps IV / VI (Eqs. 6-7) for a given g.
  *   x      n samples, binary64, host or device, contiguous.
  *   n      number of samples, n >= 2.
- *   r      derivative order, 4 or 6.
+ *   r      derivative order, 4 or 6 (Steps IV, VI), or 8 or 10 (the same
+ *          Hermite form, for plug-in stages above Algorithm 1's two).
  *   g      bandwidth > 0, in the units of x.
  *   prec   KDE_FP32 or KDE_FP64.
  *   out    one double, host or device: psi_r(g).  With a device `out` the call is
@@ -138,6 +152,19 @@ KDE_API kde_status kde_plugin_h_f32(const float* x, int64_t n, kde_precision pre
  */
 KDE_API kde_status kde_plugin_h_batch(const double* x_packed, const int64_t* offsets, int64_t m,
                               kde_precision prec, kde_result* out, void* stream);
+
+/*
+ * kde_plugin_h_stages -- the l-stage direct plug-in, of which Algorithm 1 is
+ * the case l = 2: psi_{2l+4} by the normal scale (Step II's formula for general
+ * even order), then for r = 2l+2, ..., 4 the pilot bandwidth
+ * g_r = (-2 K^(r)(0) / (mu2 psi_{r+2} n))^(1/(r+3)) (the form of Steps III and
+ * V) and psi_r(g_r) (Steps IV and VI), then h (Step VII).
+ *   stages  l in 1..4 (orders up to psi_10 are estimated from the data).
+ *   out     one kde_stage_result, host or device (device: asynchronous).
+ * Errors as kde_plugin_h; out->status holds the sample's status.
+ */
+KDE_API kde_status kde_plugin_h_stages(const double* x, int64_t n, int stages, kde_precision prec,
+                                       kde_stage_result* out, void* stream);
 
 /*
  * kde_psi_slots -- verification view of kde_psi: the per-chunk partial sums the
@@ -227,7 +254,7 @@ KDE_API kde_status kde_tile_config(kde_precision prec, int64_t n, int32_t* info)
  * Concurrency: one scratch area per device; calls that overlap on the device
  * (other streams or host threads) race on it -- order them on one stream.
  * Errors: KDE_ERR_INVALID for n > KDE_STATIC_MAX_N (message says so), n < 2,
- * r not in {4, 6}, g <= 0 or not finite, null pointers, a bad precision.
+ * r not in {4, 6, 8, 10}, g <= 0 or not finite, null pointers, a bad precision.
  */
 KDE_API kde_status kde_psi_static(const double* x, int64_t n, int r, double g, kde_precision prec,
                                   double* out, void* stream);

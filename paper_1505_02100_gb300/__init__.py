@@ -38,6 +38,18 @@ class KdeResult(ctypes.Structure):
         return d
 
 
+class KdeStageResult(ctypes.Structure):
+    _fields_ = [("mean", ctypes.c_double), ("sigma", ctypes.c_double),
+                ("psi", ctypes.c_double * 6), ("g", ctypes.c_double * 6), ("h", ctypes.c_double),
+                ("stages", ctypes.c_int32), ("status", ctypes.c_int32)]
+
+    def as_dict(self):
+        return {"mean": self.mean, "sigma": self.sigma, "h": self.h, "stages": self.stages,
+                "status": self.status,
+                "psi": {2 * k + 4: self.psi[k] for k in range(6)},
+                "g": {2 * k + 4: self.g[k] for k in range(6)}}
+
+
 class KdeServerConfig(ctypes.Structure):
     _fields_ = [("hbm_budget_bytes", ctypes.c_size_t), ("max_inflight", ctypes.c_int32),
                 ("device", ctypes.c_int32), ("tick_target_ms", ctypes.c_double)]
@@ -61,6 +73,7 @@ SIGNATURES = {
     "kde_plugin_h": (_i32, [_vp, _i64, ctypes.c_int, _vp, _vp]),
     "kde_plugin_h_f32": (_i32, [_vp, _i64, ctypes.c_int, _vp, _vp]),
     "kde_plugin_h_batch": (_i32, [_vp, _vp, _i64, ctypes.c_int, _vp, _vp]),
+    "kde_plugin_h_stages": (_i32, [_vp, _i64, ctypes.c_int, ctypes.c_int, _vp, _vp]),
     "kde_psi_slots": (_i32, [_vp, _i64, ctypes.c_int, _d, ctypes.c_int, _vp, _i64, _vp]),
     "kde_psi_static": (_i32, [_vp, _i64, ctypes.c_int, _d, ctypes.c_int, _vp, _vp]),
     "kde_eval": (_i32, [_vp, _i64, _d, _vp, _i64, ctypes.c_int, _vp, _vp]),
@@ -239,6 +252,20 @@ def kde_plugin_h(x, prec: int = KDE_FP32, out=None, stream=None, check: bool = T
         return None
     res = KdeResult()
     st = fn(p, n, int(prec), ctypes.addressof(res), _stream(stream))
+    if check and st not in (KDE_OK, KDE_ERR_DEGENERATE, KDE_ERR_DOMAIN):
+        _check(st)
+    return res.as_dict()
+
+
+def kde_plugin_h_stages(x, stages: int, prec: int = KDE_FP32, out=None, stream=None, check: bool = True):
+    """The l-stage direct plug-in (l = stages, 1..4; 2 is Algorithm 1).  Returns a dict
+    with psi / g keyed by the order r, or None with a CUDA `out` tensor (asynchronous)."""
+    p, n, keep = _buf(x, np.float64)
+    if out is not None:
+        _check(load().kde_plugin_h_stages(p, n, int(stages), int(prec), out.data_ptr(), _stream(stream)))
+        return None
+    res = KdeStageResult()
+    st = load().kde_plugin_h_stages(p, n, int(stages), int(prec), ctypes.addressof(res), _stream(stream))
     if check and st not in (KDE_OK, KDE_ERR_DEGENERATE, KDE_ERR_DOMAIN):
         _check(st)
     return res.as_dict()

@@ -87,6 +87,7 @@ SampleDesc make_desc(int prec, int cfg, int64_t n, double g_fixed) {
   d.g_fixed = g_fixed;
   d.prec = prec;
   d.cfg = cfg;
+  d.stages = 2;
   if (n < 2) return d;
   const int64_t T = pair_config(prec, cfg).tile();
   d.nt = (n + T - 1) / T;
@@ -100,7 +101,7 @@ SampleDesc make_desc(int prec, int cfg, int64_t n, double g_fixed) {
   return d;
 }
 
-enum Mode { kPlugin = 0, kPsi4 = 4, kPsi6 = 6 };
+enum Mode { kPlugin = 0 };   // or the order r of a stand-alone psi_r(g)
 
 struct Group {
   int cfg = 0;
@@ -112,6 +113,7 @@ struct Group {
 struct BatchPlan {
   int prec = KDE_FP32;
   int mode = kPlugin;
+  int stages = 2;                 // plug-in stages (2: Algorithm 1)
   int x_f32 = 0;
   std::vector<SampleDesc> desc;
   std::vector<int64_t> mprefix;
@@ -122,7 +124,7 @@ struct BatchPlan {
   uint64_t key = 0;
 
   int n_pair_launches() const {
-    return static_cast<int>(groups.size()) * (mode == kPlugin ? 2 : 1);
+    return static_cast<int>(groups.size()) * (mode == kPlugin ? stages : 1);
   }
 };
 
@@ -144,9 +146,10 @@ int num_sms() {
 
 // ns[k] sample sizes; offsets into the packed x are cumulative.
 void build_plan(BatchPlan& P, int prec, int mode, int x_f32, const int64_t* ns, int64_t m,
-                double g_fixed) {
+                double g_fixed, int stages = 2) {
   P.prec = prec;
   P.mode = mode;
+  P.stages = stages;
   P.x_f32 = x_f32;
   P.desc.resize(m);
   P.mprefix.assign(m + 1, 0);
@@ -157,6 +160,7 @@ void build_plan(BatchPlan& P, int prec, int mode, int x_f32, const int64_t* ns, 
   for (int64_t k = 0; k < m; ++k) {
     const int cfg = choose_config(prec, ns[k]);
     SampleDesc d = make_desc(prec, cfg, ns[k], g_fixed);
+    d.stages = stages;
     d.x_off = x_off;
     d.y_off = x_off;
     d.tmp_off = x_off;   // the sort's scratch is the y buffer, same offsets
@@ -203,6 +207,7 @@ void build_plan(BatchPlan& P, int prec, int mode, int x_f32, const int64_t* ns, 
   uint64_t h = 1469598103934665603ull;
   h = fnv(h, &prec, sizeof prec);
   h = fnv(h, &mode, sizeof mode);
+  h = fnv(h, &stages, sizeof stages);
   h = fnv(h, &x_f32, sizeof x_f32);
   h = fnv(h, &m, sizeof m);
   h = fnv(h, &g_fixed, sizeof g_fixed);
@@ -398,15 +403,19 @@ kde_status enqueue(Workspace& W, const BatchPlan& P, cudaStream_t s) {
   pr.ids = nullptr;
   pr.m = m;
   pr.y = W.y.p;
-  std::vector<int> orders;
-  if (P.mode == kPlugin) orders = {6, 4};
-  else orders = {P.mode};
+  std::vector<int> orders;   // the plug-in's estimated orders, top first
+  if (P.mode == kPlugin)
+    for (int r = 2 * P.stages + 2; r >= 4; r -= 2) orders.push_back(r);
+  else
+    orders = {P.mode};
   int L = 0;
   for (size_t o = 0; o < orders.size(); ++o) {
     const int r = orders[o];
     KDE_CU(launch_prescale(pr, P.bprefix[m], s));
     launches += P.bprefix[m] > 0 ? 1 : 0;
-    if (prof) KDE_CU(prof_record(W.prof[o == 0 ? 1 : 3], s));
+    const bool first = o == 0, last = o + 1 == orders.size();
+    if (prof && first) KDE_CU(prof_record(W.prof[1], s));
+    if (prof && last && !first) KDE_CU(prof_record(W.prof[3], s));
     for (const Group& g : P.groups) {
       PairArgs pa{};
       pa.y = W.y.p;
@@ -422,7 +431,12 @@ kde_status enqueue(Workspace& W, const BatchPlan& P, cudaStream_t s) {
       launches += g.grid > 0 ? 1 : 0;
       ++L;
     }
-    if (prof) KDE_CU(prof_record(W.prof[o == 0 ? 2 : 4], s));
+    if (prof && first) KDE_CU(prof_record(W.prof[2], s));
+    if (prof && last && !first) KDE_CU(prof_record(W.prof[4], s));
+  }
+  if (P.mode == kPlugin) {
+    KDE_CU(launch_stage_results(state, m, s));
+    launches += m > 0 ? 1 : 0;
   }
   if (prof && orders.size() == 1) {
     KDE_CU(prof_record(W.prof[3], s));
@@ -519,11 +533,35 @@ kde_status plugin_one(const void* x, int x_f32, int64_t n, kde_precision prec, k
   return KDE_OK;
 }
 
+kde_status plugin_stages_one(const double* x, int64_t n, int stages, kde_precision prec,
+                             kde_stage_result* out, void* stream) {
+  if (!x || !out) return set_err(KDE_ERR_INVALID, "null pointer");
+  if (n < 2) return set_err(KDE_ERR_INVALID, "n < 2");
+  if (stages < 1 || stages > 4) return set_err(KDE_ERR_INVALID, "stages must be 1..4");
+  if (prec != KDE_FP32 && prec != KDE_FP64) return set_err(KDE_ERR_INVALID, "bad precision");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  Workspace* W = nullptr;
+  kde_status st = get_workspace(s, &W);
+  if (st != KDE_OK) return st;
+  std::lock_guard<std::mutex> lk(W->mu);
+  BatchPlan P;
+  build_plan(P, prec, kPlugin, 0, &n, 1, 0.0, stages);
+  if ((st = run_plan(*W, P, x, is_device_ptr(x), s)) != KDE_OK) return st;
+  const bool out_dev = is_device_ptr(out);
+  const auto* src = &static_cast<const SampleState*>(W->state.p)->sres;
+  KDE_CU(cudaMemcpyAsync(out, src, sizeof(kde_stage_result),
+                         out_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));
+  if (out_dev) return KDE_OK;
+  KDE_CU(cudaStreamSynchronize(s));
+  if (out->status != KDE_OK) return set_err(static_cast<kde_status>(out->status), "plug-in failed on device");
+  return KDE_OK;
+}
+
 kde_status psi_run(const double* x, int64_t n, int r, double g, kde_precision prec, Workspace** Wout,
                    cudaStream_t s, BatchPlan& P) {
   if (!x) return set_err(KDE_ERR_INVALID, "null pointer");
   if (n < 2) return set_err(KDE_ERR_INVALID, "n < 2");
-  if (r != 4 && r != 6) return set_err(KDE_ERR_INVALID, "r must be 4 or 6");
+  if (r != 4 && r != 6 && r != 8 && r != 10) return set_err(KDE_ERR_INVALID, "r must be 4, 6, 8 or 10");
   if (!(g > 0) || !std::isfinite(g)) return set_err(KDE_ERR_INVALID, "g must be finite and > 0");
   if (prec != KDE_FP32 && prec != KDE_FP64) return set_err(KDE_ERR_INVALID, "bad precision");
   kde_status st = get_workspace(s, Wout);
@@ -579,6 +617,11 @@ kde_status kde_psi_slots(const double* x, int64_t n, int r, double g, kde_precis
   if ((st = run_plan(*W, P, x, is_device_ptr(x), nullptr)) != KDE_OK) return st;
   KDE_CU(cudaMemcpy(slots, W->slots.p, static_cast<size_t>(d.nchunks) * sizeof(double), cudaMemcpyDeviceToHost));
   return KDE_OK;
+}
+
+kde_status kde_plugin_h_stages(const double* x, int64_t n, int stages, kde_precision prec,
+                               kde_stage_result* out, void* stream) {
+  return plugin_stages_one(x, n, stages, prec, out, stream);
 }
 
 kde_status kde_plugin_h(const double* x, int64_t n, kde_precision prec, kde_result* out, void* stream) {

@@ -67,6 +67,8 @@ struct SampleDesc {
   double g_fixed;    // > 0: stand-alone psi_r(g) at this g; else Algorithm 1 (g1 from Step III)
   int32_t prec;      // kde_precision of this sample's pair terms
   int32_t cfg;       // pair-kernel tile configuration
+  int32_t stages;    // plug-in stages l (2: Algorithm 1); unused for a stand-alone psi_r(g)
+  int32_t reserved;
 };
 
 struct SampleState {
@@ -84,6 +86,7 @@ struct SampleState {
   uint32_t done_mom;   // moments blocks finished (reset by the last one)
   uint32_t done_pairs; // chunks finished (reset by the last one)
   unsigned long long skipped[2];   // unique pairs in far tile pairs not evaluated: psi6, psi4
+  kde_stage_result sres;           // l-stage results (psi_r, pilots) as the plug-in proceeds
 };
 
 struct MomentsArgs {
@@ -116,8 +119,8 @@ struct PairArgs {
   int64_t n_items;
   double* slots;
   unsigned long long* counters;
-  int r;                   // 4 or 6
-  int chain;               // 1: Algorithm 1 (r = 6 -> Step V, r = 4 -> Step VII)
+  int r;                   // 4, 6, 8 or 10
+  int chain;               // 1: plug-in chain (r > 4 -> next pilot, r = 4 -> Step VII)
 };
 
 constexpr int kPrescaleThreads = 256;
@@ -148,6 +151,7 @@ cudaError_t launch_prescale(const PrescaleArgs& a, int64_t total_blocks, cudaStr
 // Sorts each sample's values in x in place (tmp: scratch of the same size).
 cudaError_t launch_sort(const SortArgs& a, int64_t total_blocks, void* x, void* tmp, cudaStream_t s);
 cudaError_t launch_pairs(int prec, int cfg, const PairArgs& a, int grid, cudaStream_t s);
+cudaError_t launch_stage_results(SampleState* state, int64_t m, cudaStream_t s);
 // Resident CTAs per SM of a pair configuration (occupancy query, cached).
 int pair_blocks_per_sm(int prec, int cfg);
 

@@ -133,6 +133,48 @@ __device__ bool set_psi_scale(SampleState* st, double g, int prec) {
   return true;
 }
 
+// K^(r)(0) = He_r(0) / sqrt(2 pi)
+__device__ __forceinline__ double kernel_deriv_at_zero(int r) {
+  return (r == 4 ? 3.0 : r == 6 ? -15.0 : r == 8 ? 105.0 : r == 10 ? -945.0 : 10395.0) /
+         sqrt(2.0 * kPi);
+}
+
+// psi_r by the normal scale (Step II's formula for general even r):
+// (-1)^(r/2) r! / ((2 sigma)^(r+1) (r/2)! sqrt(pi)).
+__device__ __forceinline__ double normal_scale_psi(int r, double sigma) {
+  double num = 1.0, den = 1.0;
+  for (int k = 2; k <= r; ++k) num *= k;
+  for (int k = 2; k <= r / 2; ++k) den *= k;
+  const double v = num / (pow(2.0 * sigma, r + 1.0) * den * sqrt(kPi));
+  return (r / 2) % 2 ? -v : v;
+}
+
+// Record psi_r (and the pilot it was taken at) in the stage results and in the
+// Algorithm-1 fields that correspond to it.
+__device__ __forceinline__ void record_psi(SampleState* st, int r, double psi, double g) {
+  st->sres.psi[r / 2 - 2] = psi;
+  st->sres.g[r / 2 - 2] = g;
+  if (r == 8) st->res.psi8 = psi;
+  if (r == 6) { st->res.psi6 = psi; st->res.g1 = g; }
+  if (r == 4) { st->res.psi4 = psi; st->res.g2 = g; }
+}
+
+// Pilot bandwidth for psi_r from psi_{r+2} (Steps III and V, mu2 = 1); sets the
+// scale of the next pair launch.  false (DOMAIN) if the ratio is not positive.
+template <int PREC>
+__device__ bool next_pilot(SampleState* st, int r, double psi_up, double n) {
+  const double ratio = -2.0 * kernel_deriv_at_zero(r) / (psi_up * n);
+  if (!(ratio > 0.0)) {
+    st->res.status = KDE_ERR_DOMAIN;
+    return false;
+  }
+  const double g = pow(ratio, 1.0 / (r + 3.0));
+  st->sres.g[r / 2 - 2] = g;
+  if (r == 6) st->res.g1 = g;
+  if (r == 4) st->res.g2 = g;
+  return set_psi_scale(st, g, PREC);
+}
+
 // ---------------------------------------------------------------------------
 // init: every result field NaN, status OK (or INVALID for n < 2), counters 0
 // ---------------------------------------------------------------------------
@@ -153,6 +195,20 @@ __global__ void init_states_kernel(const SampleDesc* desc, SampleState* state, i
   st->done_mom = 0;
   st->done_pairs = 0;
   st->skipped[0] = st->skipped[1] = 0;
+  st->sres.mean = st->sres.sigma = st->sres.h = CUDART_NAN;
+  for (int q = 0; q < 6; ++q) st->sres.psi[q] = st->sres.g[q] = CUDART_NAN;
+  st->sres.stages = desc[k].stages;
+}
+
+// The l-stage result of each sample from its state (after the last pair launch).
+__global__ void stage_results_kernel(SampleState* state, int64_t m) {
+  const int64_t k = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
+  if (k >= m) return;
+  SampleState* st = state + k;
+  st->sres.mean = st->res.mean;
+  st->sres.sigma = st->res.sigma;
+  st->sres.h = st->res.h;
+  st->sres.status = st->res.status;
 }
 
 // ---------------------------------------------------------------------------
@@ -266,12 +322,16 @@ __global__ void __launch_bounds__(kMomThreads) moments_kernel(MomentsArgs a) {
       st->res.status = KDE_ERR_DEGENERATE;
       return;
     }
-    const double psi8 = 105.0 / (32.0 * sqrt(kPi) * pow(sigma, 9.0));   // Step II
-    const double k6_0 = -15.0 / sqrt(2.0 * kPi);                          // K^(6)(0)
-    const double g1 = pow(-2.0 * k6_0 / (psi8 * n), 1.0 / 9.0);           // Step III, mu2 = 1
-    st->res.psi8 = psi8;
-    st->res.g1 = g1;
-    g = g1;
+    // Step II: the top functional by the normal scale (psi_8 for Algorithm 1's
+    // two stages, psi_{2l+4} for l stages); Step III: the first pilot
+    const int top = 2 * d.stages + 4;
+    const double psi_ns = normal_scale_psi(top, sigma);
+    st->sres.psi[top / 2 - 2] = psi_ns;
+    if (top == 8) st->res.psi8 = psi_ns;
+    if (top == 6) st->res.psi6 = psi_ns;
+    if (d.prec == KDE_FP32) next_pilot<KDE_FP32>(st, top - 2, psi_ns, n);
+    else next_pilot<KDE_FP64>(st, top - 2, psi_ns, n);
+    return;
   }
   set_psi_scale(st, g, d.prec);
 }
@@ -332,23 +392,43 @@ constexpr int kFLo = 16;
 // like (sigma/g)^6, ~1e4 at n = 2^20) that binary32 would lose several digits.
 template <typename T, int RORD>
 struct Coef {
-  T c3, c2, c1, c0;
+  // Horner coefficients, highest power first.  r <= 6: polynomial in v with the
+  // powers of p2 folded in (exact: integers times powers of two).  r >= 8:
+  // polynomial in w = v p2 = u^2 (integer coefficients), because p2^(r/2)
+  // would leave the binary32 range for fine grids.
+  static constexpr int K = RORD / 2 + 1;
+  static constexpr bool kOnW = RORD >= 8;
+  T c[K];
   // h = 1 or 1/2; p2 = 2^(-2F) turns v in grid units into u^2 (exact)
   __device__ void set(double h, double p2) {
-    const double p4 = p2 * p2, p6 = p4 * p2;
-    if (RORD == 6) {
-      c3 = static_cast<T>(h * p6);
-      c2 = static_cast<T>(-15.0 * h * p4);
-      c1 = static_cast<T>(45.0 * h * p2);
-      c0 = static_cast<T>(-15.0 * h);
-    } else {
-      c3 = static_cast<T>(0);
-      c2 = static_cast<T>(h * p4);
-      c1 = static_cast<T>(-6.0 * h * p2);
-      c0 = static_cast<T>(3.0 * h);
+    // He_r(u) = sum_k a[k] u^(2 (K-1-k)), coefficients of the Hermite forms
+    // printed in Steps IV and VI and their continuation for r = 8, 10
+    const double a4[3] = {1.0, -6.0, 3.0};
+    const double a6[4] = {1.0, -15.0, 45.0, -15.0};
+    const double a8[5] = {1.0, -28.0, 210.0, -420.0, 105.0};
+    const double a10[6] = {1.0, -45.0, 630.0, -3150.0, 4725.0, -945.0};
+    const double* a = RORD == 4 ? a4 : RORD == 6 ? a6 : RORD == 8 ? a8 : a10;
+    for (int k = 0; k < K; ++k) {
+      double scale = h;
+      if (!kOnW)
+        for (int e = 0; e < K - 1 - k; ++e) scale *= p2;
+      c[k] = static_cast<T>(a[k] * scale);
     }
   }
+  template <typename U>
+  __device__ __forceinline__ U horner(U x) const {   // x = v (r <= 6) or w (r >= 8)
+    U p = c[0];
+#pragma unroll
+    for (int k = 1; k < K; ++k) p = fma(p, x, c[k]);
+    return p;
+  }
 };
+
+// He_r(0) for the diagonal: (-1)^(r/2) (r - 1)!!
+template <int RORD>
+__host__ __device__ constexpr double he_at_zero() {
+  return RORD == 4 ? 3.0 : RORD == 6 ? -15.0 : RORD == 8 ? 105.0 : -945.0;
+}
 
 // exp(-u^2/2) in binary32 on the FMA pipe, as 2^t with t = -u^2 / (2 ln 2).
 // In grid units t = -v c with c = 2^(-2F) / (2 ln 2) = c_hi + c_lo split into
@@ -400,15 +480,13 @@ __device__ __forceinline__ float exp2_reduced(float f) {
 // `vout` receives v: the term is too large by the relative amount v c_lo ln 2.
 template <int RORD, bool CLAMP>
 __device__ __forceinline__ float term32(float d, const Coef<float, RORD>& cf, float c_hi, float vmax,
-                                        float& vout) {
+                                        float p2f, float& vout) {
   const float v = CLAMP ? fminf(__fmul_rn(d, d), vmax) : __fmul_rn(d, d);
   const float yb = __fmaf_rn(v, -c_hi, kRoundMagic);      // low bits: k = round(t)
   const float kf = __fsub_rn(yb, kRoundMagic);
   const float f = __fmaf_rn(v, -c_hi, -kf);               // t - k (c_hi part)
   const float e = __int_as_float(__float_as_int(exp2_reduced(f)) + (__float_as_int(yb) << 23));
-  float p;
-  if (RORD == 6) p = __fmaf_rn(__fmaf_rn(__fmaf_rn(cf.c3, v, cf.c2), v, cf.c1), v, cf.c0);
-  else p = __fmaf_rn(__fmaf_rn(cf.c2, v, cf.c1), v, cf.c0);
+  const float p = Coef<float, RORD>::kOnW ? cf.horner(__fmul_rn(v, p2f)) : cf.horner(v);
   vout = v;
   return __fmul_rn(p, e);
 }
@@ -418,9 +496,7 @@ __device__ __forceinline__ double term64(double a, double b, const Coef<double, 
                                          double acc) {
   const double d = __dsub_rn(a, b);
   const double v = __dmul_rn(d, d);
-  double p;
-  if (RORD == 6) p = fma(fma(fma(cf.c3, v, cf.c2), v, cf.c1), v, cf.c0);
-  else p = fma(fma(cf.c2, v, cf.c1), v, cf.c0);
+  const double p = cf.horner(v);   // u-units: v = u^2 = w
   return fma(p, exp(-0.5 * v), acc);
 }
 
@@ -450,7 +526,7 @@ template <int RORD, int ROWS, int CJ, int TILE, bool CLAMP, bool LO>
 __device__ __forceinline__ void tile_pass(const float* __restrict__ tile, const float* __restrict__ tile_lo,
                                           const float (&w)[ROWS], const float (&wl)[ROWS],
                                           const Coef<float, RORD>& cf, float c_hi, double c_lo_ln2,
-                                          float vmax, Kahan32& acc, double& cacc) {
+                                          float vmax, float p2f, Kahan32& acc, double& cacc) {
   static_assert(CJ == 4, "one float4 of columns per group of terms");
   float sum[ROWS], comp[ROWS], tv[ROWS];
 #pragma unroll
@@ -475,7 +551,7 @@ __device__ __forceinline__ void tile_pass(const float* __restrict__ tile, const 
         float v;
         // grid difference (exact), plus the residuals when the grid is coarse
         const float d = LO ? __fadd_rn(__fsub_rn(w[r], b[q]), __fsub_rn(wl[r], bl[q])) : __fsub_rn(w[r], b[q]);
-        t[q] = term32<RORD, CLAMP>(d, cf, c_hi, vmax, v);
+        t[q] = term32<RORD, CLAMP>(d, cf, c_hi, vmax, p2f, v);
         tv[r] = __fmaf_rn(t[q], v, tv[r]);
       }
       const float g4 = __fadd_rn(__fadd_rn(t[0], t[1]), __fadd_rn(t[2], t[3]));
@@ -543,40 +619,43 @@ __device__ void finalize_pairs(const PairArgs& a, const SampleDesc& d, SampleSta
   if (st->res.status != KDE_OK) return;
   const double n = static_cast<double>(d.n);
   const double g = st->g_cur;
-  const double he0 = RORD == 6 ? -15.0 : 3.0;
   // Eqs. 6-7: [2 sum_{i<j} K^(r) + n K^(r)(0)] / (n^2 g^(r+1)), K^(r) = He_r phi
-  const double psi = (2.0 * s + n * he0) / (sqrt(2.0 * kPi) * n * n * pow(g, RORD + 1.0));
+  const double psi = (2.0 * s + n * he_at_zero<RORD>()) / (sqrt(2.0 * kPi) * n * n * pow(g, RORD + 1.0));
   if (!a.chain) {
     st->psi_out = psi;
-    if (RORD == 6) st->res.psi6 = psi; else st->res.psi4 = psi;
+    if (RORD == 6) st->res.psi6 = psi;
+    if (RORD == 4) st->res.psi4 = psi;
     return;
   }
-  if (RORD == 6) {
-    st->res.psi6 = psi;
-    if (!(psi < 0.0)) { st->res.status = KDE_ERR_DOMAIN; return; }
-    const double k4_0 = 3.0 / sqrt(2.0 * kPi);                 // K^(4)(0)
-    const double g2 = pow(-2.0 * k4_0 / (psi * n), 1.0 / 7.0); // Step V, mu2 = 1
-    st->res.g2 = g2;
-    set_psi_scale(st, g2, PREC);
-  } else {
-    st->res.psi4 = psi;
-    if (!(psi > 0.0)) { st->res.status = KDE_ERR_DOMAIN; return; }
-    const double RK = 1.0 / (2.0 * sqrt(kPi));                 // R(K)
-    st->res.h = pow(RK / (psi * n), 1.0 / 5.0);                 // Step VII, mu2 = 1
+  record_psi(st, RORD, psi, g);
+  if (RORD > 4) {
+    next_pilot<PREC>(st, RORD - 2, psi, n);   // Steps V (and their continuation above)
+    return;
   }
+  if (!(psi > 0.0)) {
+    st->res.status = KDE_ERR_DOMAIN;
+    return;
+  }
+  const double RK = 1.0 / (2.0 * sqrt(kPi));                 // R(K)
+  st->res.h = pow(RK / (psi * n), 1.0 / 5.0);                 // Step VII, mu2 = 1
 }
 
-// Register budget per thread: binary32 64 with 4 rows (the fast path needs no
-// more), 96 with 8; binary64 128 (its inlined exp would otherwise take ~170).
-template <int PREC, int THREADS, int ROWS>
+// Register budget per thread: binary32 64 with 4 rows and r <= 6 (the fast
+// path needs no more), 96 with 8 rows or r >= 8; binary64 is left to the
+// compiler (its inlined exp takes ~170; the FP64 pipe, not occupancy, bounds it).
+template <int PREC, int ROWS, int RORD>
+constexpr int pair_reg_budget() {
+  return PREC != KDE_FP32 ? 65536 : (ROWS >= 8 || RORD >= 8) ? 96 : 64;
+}
+template <int PREC, int THREADS, int ROWS, int RORD>
 constexpr int pair_min_blocks() {
-  return 65536 / ((PREC != KDE_FP32 ? 128 : ROWS >= 8 ? 96 : 64) * THREADS) > 0
-             ? 65536 / ((PREC != KDE_FP32 ? 128 : ROWS >= 8 ? 96 : 64) * THREADS)
+  return 65536 / (pair_reg_budget<PREC, ROWS, RORD>() * THREADS) > 0
+             ? 65536 / (pair_reg_budget<PREC, ROWS, RORD>() * THREADS)
              : 1;
 }
 
 template <int PREC, int THREADS, int ROWS, int CJ, int RORD>
-__global__ void __launch_bounds__(THREADS, (pair_min_blocks<PREC, THREADS, ROWS>())) pairs_kernel(PairArgs a) {
+__global__ void __launch_bounds__(THREADS, (pair_min_blocks<PREC, THREADS, ROWS, RORD>())) pairs_kernel(PairArgs a) {
   using T = typename Arith<PREC>::T;
   constexpr int TILE = THREADS * ROWS;
   static_assert(TILE % 8 == 0, "tile");
@@ -608,6 +687,7 @@ __global__ void __launch_bounds__(THREADS, (pair_min_blocks<PREC, THREADS, ROWS>
       const float c_hi = static_cast<float>(kInvTwoLn2 * p2);
       const double c_lo_ln2 = (kInvTwoLn2 * p2 - static_cast<double>(c_hi)) * 0.69314718055994530942;
       const float vmax = kMinT / c_hi;
+      const float p2f = static_cast<float>(p2);
       Coef<T, RORD> full, half;
       full.set(1.0, p2);
       half.set(0.5, p2);
@@ -680,11 +760,11 @@ __global__ void __launch_bounds__(THREADS, (pair_min_blocks<PREC, THREADS, ROWS>
           const double span = static_cast<double>(tile[TILE - 1]) - static_cast<double>(hi_of(y[I * TILE])) + margin;
           const bool near = (J + 1) * TILE <= d.n && span * span <= static_cast<double>(vmax);
           if (lo_path) {
-            if (near) tile_pass<RORD, ROWS, CJ, TILE, false, true>(tile, tile_lo, w, wl, cf, c_hi, c_lo_ln2, vmax, acc32, cacc);
-            else tile_pass<RORD, ROWS, CJ, TILE, true, true>(tile, tile_lo, w, wl, cf, c_hi, c_lo_ln2, vmax, acc32, cacc);
+            if (near) tile_pass<RORD, ROWS, CJ, TILE, false, true>(tile, tile_lo, w, wl, cf, c_hi, c_lo_ln2, vmax, p2f, acc32, cacc);
+            else tile_pass<RORD, ROWS, CJ, TILE, true, true>(tile, tile_lo, w, wl, cf, c_hi, c_lo_ln2, vmax, p2f, acc32, cacc);
           } else {
-            if (near) tile_pass<RORD, ROWS, CJ, TILE, false, false>(tile, tile_lo, w, wl, cf, c_hi, c_lo_ln2, vmax, acc32, cacc);
-            else tile_pass<RORD, ROWS, CJ, TILE, true, false>(tile, tile_lo, w, wl, cf, c_hi, c_lo_ln2, vmax, acc32, cacc);
+            if (near) tile_pass<RORD, ROWS, CJ, TILE, false, false>(tile, tile_lo, w, wl, cf, c_hi, c_lo_ln2, vmax, p2f, acc32, cacc);
+            else tile_pass<RORD, ROWS, CJ, TILE, true, false>(tile, tile_lo, w, wl, cf, c_hi, c_lo_ln2, vmax, p2f, acc32, cacc);
           }
         } else {
           tile_pass64<RORD, ROWS, TILE>(tile, w, cf, acc64);
@@ -706,8 +786,7 @@ __global__ void __launch_bounds__(THREADS, (pair_min_blocks<PREC, THREADS, ROWS>
     }
     const double tot = block_sum<THREADS>(part, red);
     if (tid == 0) {
-      const double he0 = RORD == 6 ? -15.0 : 3.0;
-      a.slots[d.slot_off + c] = tot - 0.5 * he0 * diag_units;
+      a.slots[d.slot_off + c] = tot - 0.5 * he_at_zero<RORD>() * diag_units;
       __threadfence();
       const unsigned prev = atomicAdd(&st->done_pairs, 1u);
       s_last = (prev + 1 == static_cast<unsigned>(d.nchunks));
@@ -736,11 +815,12 @@ using PairKernel = void (*)(PairArgs);
 
 struct ConfigEntry {
   PairConfig cfg;
-  PairKernel k4, k6;
+  PairKernel k4, k6, k8, k10;
 };
 
-#define KDE_CFG(P, TH, RW, CJ) \
-  { {TH, RW}, pairs_kernel<P, TH, RW, CJ, 4>, pairs_kernel<P, TH, RW, CJ, 6> }
+#define KDE_CFG(P, TH, RW, CJ)                                                       \
+  { {TH, RW}, pairs_kernel<P, TH, RW, CJ, 4>, pairs_kernel<P, TH, RW, CJ, 6>,         \
+    pairs_kernel<P, TH, RW, CJ, 8>, pairs_kernel<P, TH, RW, CJ, 10> }
 
 const ConfigEntry kFp32Configs[] = {
     KDE_CFG(KDE_FP32, 128, 4, 4),   // T = 512
@@ -783,6 +863,12 @@ int pair_blocks_per_sm(int prec, int cfg) {
   return v;
 }
 
+cudaError_t launch_stage_results(SampleState* state, int64_t m, cudaStream_t s) {
+  if (m <= 0) return cudaSuccess;
+  stage_results_kernel<<<static_cast<unsigned>((m + 255) / 256), 256, 0, s>>>(state, m);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_init(const SampleDesc* desc, SampleState* state, int64_t m,
                         unsigned long long* counters, int n_counters, cudaStream_t s) {
   const int64_t work = m > n_counters ? m : n_counters;
@@ -806,7 +892,17 @@ cudaError_t launch_prescale(const PrescaleArgs& a, int64_t total_blocks, cudaStr
 cudaError_t launch_pairs(int prec, int cfg, const PairArgs& a, int grid, cudaStream_t s) {
   if (a.n_items <= 0 || grid <= 0) return cudaSuccess;
   const ConfigEntry& e = entry(prec, cfg);
-  PairKernel k = a.r == 6 ? e.k6 : e.k4;
+  PairKernel k = a.r == 6 ? e.k6 : a.r == 8 ? e.k8 : a.r == 10 ? e.k10 : e.k4;
+  if (a.r >= 8) {   // the higher orders may hold more registers: at most their resident count
+    static int cache[2][8][2] = {};
+    int& v = cache[prec == KDE_FP32 ? 0 : 1][cfg][a.r == 8 ? 0 : 1];
+    if (v == 0) {
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, k, e.cfg.threads, 0);
+      if (v < 1) v = 1;
+    }
+    const int cap = v * num_sms();
+    if (grid > cap) grid = cap;
+  }
   k<<<grid, e.cfg.threads, 0, s>>>(a);
   return cudaGetLastError();
 }

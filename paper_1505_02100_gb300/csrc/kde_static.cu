@@ -114,7 +114,7 @@ extern "C" kde_status kde_psi_static(const double* x, int64_t n, int r, double g
     return set_err(KDE_ERR_INVALID, "kde_psi_static: n = " + std::to_string(n) +
                                         " exceeds the static scratch limit of " + std::to_string(kStaticMaxN) +
                                         " values; use kde_psi");
-  if (r != 4 && r != 6) return set_err(KDE_ERR_INVALID, "r must be 4 or 6");
+  if (r != 4 && r != 6 && r != 8 && r != 10) return set_err(KDE_ERR_INVALID, "r must be 4, 6, 8 or 10");
   if (!(g > 0) || !std::isfinite(g)) return set_err(KDE_ERR_INVALID, "g must be finite and > 0");
   if (prec != KDE_FP32 && prec != KDE_FP64) return set_err(KDE_ERR_INVALID, "bad precision");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
