@@ -89,6 +89,12 @@ def _load():
         lib.oracle_long_double_mantissa_bits.restype = ip
         lib.oracle_kde_eval.argtypes = [dp, i64, d, dp, i64, ip, dp]
         lib.oracle_plugin_stages.argtypes = [dp, i64, ip, ip, ip, ctypes.POINTER(StageResult)]
+        lib.oracle_q32_mul.argtypes = [i64, i64]
+        lib.oracle_q32_mul.restype = i64
+        lib.oracle_q32_exp_half.argtypes = [i64]
+        lib.oracle_q32_exp_half.restype = i64
+        lib.oracle_psi_q32.argtypes = [dp, i64, ip, d, d, d, ip, dp, dp]
+        lib.oracle_plugin_q32.argtypes = [dp, i64, ip, ctypes.POINTER(Result)]
         _lib = lib
     return _lib
 
@@ -194,4 +200,33 @@ def plugin_stages(x, stages: int, form: int = FORM_SYMMETRIC, threads: int | Non
     res = StageResult()
     _load().oracle_plugin_stages(_ptr(a), a.size, int(stages), int(form),
                                  int(threads or default_threads()), ctypes.byref(res))
+    return res.as_dict()
+
+
+def q32_mul(a: int, b: int) -> int:
+    """Q32.32 product (truncation toward -inf) of two raw int64 values."""
+    return _load().oracle_q32_mul(int(a), int(b))
+
+
+def q32_exp_half(w: int) -> int:
+    """floor(2^32 exp(-w/2)) for the Q32.32 raw value w >= 0."""
+    return _load().oracle_q32_exp_half(int(w))
+
+
+def psi_q32(x, r: int, g: float, mean: float, sigma: float, threads: int | None = None):
+    """(psi_r(g), sum |He_r|) with the pair sum in Q32.32 on z-scored data."""
+    a = _arr(x)
+    out, tot = ctypes.c_double(), ctypes.c_double()
+    st = _load().oracle_psi_q32(_ptr(a), a.size, int(r), float(g), float(mean), float(sigma),
+                                int(threads or default_threads()), ctypes.byref(out), ctypes.byref(tot))
+    if st != OK:
+        raise ValueError(f"oracle_psi_q32 status {st}")
+    return out.value, tot.value
+
+
+def plugin_q32(x, threads: int | None = None) -> dict:
+    """Algorithm 1 with the Steps IV / VI pair sums in Q32.32 on z-scored data (Eq. 3)."""
+    a = _arr(x)
+    res = Result()
+    _load().oracle_plugin_q32(_ptr(a), a.size, int(threads or default_threads()), ctypes.byref(res))
     return res.as_dict()

@@ -352,3 +352,137 @@ int oracle_kde_eval(const double* x, int64_t n, double h, const double* t, int64
     }
     return ORACLE_OK;
 }
+
+/* ---- Q32.32 fixed point: the paper's arithmetic (Section 4.1) for the pair terms ----- */
+/* Values are int64 raw with value = raw * 2^-32: 31 integer bits, 32 fractional bits,
+ * a sign bit.  Products keep the high part of the exact 128-bit product, i.e. they
+ * truncate toward minus infinity.  The data are z-scored first (Eq. 3), so the
+ * pair differences are in units of the sample standard deviation; u = d * sigma / g. */
+typedef int64_t q32;
+#define Q_ONE ((q32)1 << 32)
+
+q32 oracle_q32_mul(q32 a, q32 b) { return (q32)(((__int128)a * (__int128)b) >> 32); }
+
+/* floor(2^32 exp(-w / 2)) for w = w_raw * 2^-32 >= 0, in long double. */
+q32 oracle_q32_exp_half(q32 w) {
+    long double wr = (long double)w / 4294967296.0L;
+    long double e = expl(-0.5L * wr) * 4294967296.0L;
+    return (q32)floorl(e);
+}
+
+/* One pair term He_r(u) exp(-u^2/2) in Q32.32 (without 1/sqrt(2 pi)); |He_r| into *pabs.
+ * Pairs with |u| >= 64 or u^2 >= 45 give 0: there floor(2^32 exp(-u^2/2)) is already 0. */
+static q32 q32_term(int r, q32 d, q32 ginv, double* pabs) {
+    *pabs = 0.0;
+    if (fabs((double)d * (double)ginv) >= 64.0 * 18446744073709551616.0) return 0;
+    q32 u = oracle_q32_mul(d, ginv);
+    q32 w = oracle_q32_mul(u, u);
+    if (w >= 45 * Q_ONE) return 0;
+    q32 p;
+    if (r == 6) {          /* ((w - 15) w + 45) w - 15 */
+        p = oracle_q32_mul(w - 15 * Q_ONE, w) + 45 * Q_ONE;
+        p = oracle_q32_mul(p, w) - 15 * Q_ONE;
+    } else {               /* (w - 6) w + 3 */
+        p = oracle_q32_mul(w - 6 * Q_ONE, w) + 3 * Q_ONE;
+    }
+    *pabs = fabs((double)p) / 4294967296.0;
+    return oracle_q32_mul(p, oracle_q32_exp_half(w));
+}
+
+typedef struct {
+    const q32* z;
+    int64_t n;
+    int r;
+    q32 ginv;
+    __int128* row;
+    double* rowabs;
+    int64_t next;
+} q32_job;
+
+static void* q32_worker(void* arg) {
+    q32_job* jb = (q32_job*)arg;
+    for (;;) {
+        int64_t b = __atomic_fetch_add(&jb->next, 1, __ATOMIC_RELAXED);
+        int64_t i0 = b * ROW_BLOCK;
+        if (i0 >= jb->n) break;
+        int64_t i1 = i0 + ROW_BLOCK < jb->n ? i0 + ROW_BLOCK : jb->n;
+        for (int64_t i = i0; i < i1; ++i) {
+            __int128 s = 0;
+            double a = 0.0, pa;
+            for (int64_t j = i + 1; j < jb->n; ++j) {
+                s += q32_term(jb->r, jb->z[i] - jb->z[j], jb->ginv, &pa);
+                a += pa;
+            }
+            jb->row[i] = s;
+            jb->rowabs[i] = a;
+        }
+    }
+    return NULL;
+}
+
+/* psi_r(g) with the pair sum of Eqs. (6)-(7) in Q32.32 on z = (x - mean) / sigma
+ * (z truncated to Q32.32), everything else in binary64.  *sum_abs_he receives
+ * sum_{i<j} |He_r(u_ij)| (in the same units as the terms) for error bounds. */
+int oracle_psi_q32(const double* x, int64_t n, int r, double g, double mean, double sigma,
+                   int nthreads, double* psi, double* sum_abs_he) {
+    if (!x || !psi || n < 1 || (r != 4 && r != 6) || !(g > 0) || !(sigma > 0)) return ORACLE_ERR_INVALID;
+    q32* z = (q32*)malloc(sizeof(q32) * (size_t)n);
+    __int128* row = (__int128*)malloc(sizeof(__int128) * (size_t)n);
+    double* rowabs = (double*)malloc(sizeof(double) * (size_t)n);
+    if (!z || !row || !rowabs) { free(z); free(row); free(rowabs); return ORACLE_ERR_INVALID; }
+    for (int64_t i = 0; i < n; ++i) {
+        double zi = (x[i] - mean) / sigma;                        /* Eq. (3) */
+        if (!(fabs(zi) < 536870912.0)) { free(z); free(row); free(rowabs); return ORACLE_ERR_INVALID; }
+        z[i] = (q32)floor(zi * 4294967296.0);
+    }
+    q32_job jb = {z, n, r, (q32)floor(sigma / g * 4294967296.0), row, rowabs, 0};
+    if (nthreads < 1) nthreads = 1;
+    if (nthreads > 1024) nthreads = 1024;
+    if (nthreads == 1) {
+        q32_worker(&jb);
+    } else {
+        pthread_t th[1024];
+        int started = 0;
+        for (int t = 0; t < nthreads; ++t)
+            if (pthread_create(&th[t], NULL, q32_worker, &jb) == 0) ++started;
+        if (started == 0) q32_worker(&jb);
+        for (int t = 0; t < started; ++t) pthread_join(th[t], NULL);
+    }
+    __int128 tot = 0;
+    double abs_tot = 0.0;
+    for (int64_t i = 0; i < n; ++i) { tot += row[i]; abs_tot += rowabs[i]; }
+    free(z); free(row); free(rowabs);
+    double he0 = (r == 6) ? -15.0 : 3.0;
+    double nn = (double)n;
+    double s = (double)tot / 4294967296.0;                        /* sum_{i<j} He_r exp(-u^2/2) */
+    *psi = (2.0 * s + nn * he0) * inv_sqrt_2pi() / (nn * nn * pow(g, (double)(r + 1)));
+    if (sum_abs_he) *sum_abs_he = abs_tot;
+    return ORACLE_OK;
+}
+
+/* Algorithm 1 with the pair sums of Steps IV and VI in Q32.32 on z-scored data
+ * (Eq. 3), the scalar steps in binary64; h comes out in the units of x (Eq. 4). */
+int oracle_plugin_q32(const double* x, int64_t n, int nthreads, oracle_result* out) {
+    if (!out) return ORACLE_ERR_INVALID;
+    fill_nan(out);
+    out->status = ORACLE_ERR_INVALID;
+    if (!x || n < 2) return out->status;
+    double nn = (double)n, mean, var;
+    int st = oracle_moments(x, n, &mean, &var);
+    if (st != ORACLE_OK) { out->status = st; return st; }
+    out->mean = mean;
+    out->sigma = sqrt(var);
+    if (!(out->sigma > 0)) { out->status = ORACLE_ERR_DEGENERATE; return out->status; }
+    out->psi8 = 105.0 / (32.0 * sqrt(PI) * pow(out->sigma, 9.0));
+    out->g1 = pow(-2.0 * (-15.0 * inv_sqrt_2pi()) / (out->psi8 * nn), 1.0 / 9.0);
+    st = oracle_psi_q32(x, n, 6, out->g1, mean, out->sigma, nthreads, &out->psi6, NULL);
+    if (st != ORACLE_OK) { out->status = st; return st; }
+    if (!(out->psi6 < 0)) { out->status = ORACLE_ERR_DOMAIN; return out->status; }
+    out->g2 = pow(-2.0 * (3.0 * inv_sqrt_2pi()) / (out->psi6 * nn), 1.0 / 7.0);
+    st = oracle_psi_q32(x, n, 4, out->g2, mean, out->sigma, nthreads, &out->psi4, NULL);
+    if (st != ORACLE_OK) { out->status = st; return st; }
+    if (!(out->psi4 > 0)) { out->status = ORACLE_ERR_DOMAIN; return out->status; }
+    out->h = pow(1.0 / (2.0 * sqrt(PI)) / (out->psi4 * nn), 1.0 / 5.0);
+    out->status = ORACLE_OK;
+    return ORACLE_OK;
+}

@@ -91,6 +91,20 @@ int oracle_long_double_mantissa_bits(void);
 int oracle_kde_eval(const double* x, int64_t n, double h, const double* t, int64_t m,
                     int nthreads, double* out);
 
+/* Q32.32 fixed point (Section 4.1): int64 raw, value = raw * 2^-32; products
+ * keep the high part of the exact 128-bit product (truncation toward -inf). */
+int64_t oracle_q32_mul(int64_t a, int64_t b);
+/* floor(2^32 exp(-w/2)) for the Q32.32 value w >= 0 (long double). */
+int64_t oracle_q32_exp_half(int64_t w);
+/* psi_r(g), r in {4, 6}, with the pair sum in Q32.32 on z = (x - mean)/sigma
+ * (Eq. 3, truncated to Q32.32), u = z-difference * (sigma/g) in Q32.32; the
+ * exponential is the exactly truncated value.  *sum_abs_he (may be NULL) gets
+ * sum_{i<j} |He_r(u_ij)| for error bounds. */
+int oracle_psi_q32(const double* x, int64_t n, int r, double g, double mean, double sigma,
+                   int nthreads, double* psi, double* sum_abs_he);
+/* Algorithm 1 with the Steps IV / VI pair sums in Q32.32 (as oracle_psi_q32). */
+int oracle_plugin_q32(const double* x, int64_t n, int nthreads, oracle_result* out);
+
 #ifdef __cplusplus
 }
 #endif
