@@ -410,7 +410,10 @@ static void* q32_worker(void* arg) {
             __int128 s = 0;
             double a = 0.0, pa;
             for (int64_t j = i + 1; j < jb->n; ++j) {
-                s += q32_term(jb->r, jb->z[i] - jb->z[j], jb->ginv, &pa);
+                /* K^(r) is even (Eq. 5), but a truncating product is not odd in its
+                   operand: the term is taken on the magnitude of the difference. */
+                q32 dz = jb->z[i] - jb->z[j];
+                s += q32_term(jb->r, dz < 0 ? -dz : dz, jb->ginv, &pa);
                 a += pa;
             }
             jb->row[i] = s;
