@@ -428,6 +428,30 @@ def run_ours(args, ws, rank, local):
                 "pairs6_ms": statistics.mean(k6_64), "pairs4_ms": statistics.mean(k4_64),
                 "h": res64["h"]}
 
+    # the paper's Q32.32 arithmetic on the same workload (a few steps)
+    q32 = None
+    if not args.no_fp64:
+        kq = 3
+        kde.kde_profile_enable(True)
+        kde.kde_plugin_h(xd, kde.KDE_Q32, out=out, stream=stream)
+        tq_prof = kde.kde_profile_last(stream)
+        kde.kde_profile_enable(False)
+        q_skipped = tq_prof["skipped6"] + tq_prof["skipped4"]
+        qe = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(kq)]
+        for i in range(kq):
+            with torch.cuda.stream(stream):
+                flush.zero_()
+            qe[i][0].record(stream)
+            kde.kde_plugin_h(xd, kde.KDE_Q32, out=out, stream=stream)
+            qe[i][1].record(stream)
+        stream.synchronize()
+        tq = sum(a.elapsed_time(b) for a, b in qe) / 1e3 / kq
+        resq = kde.kde_plugin_h(xd, kde.KDE_Q32)
+        q32 = {"pair_evals_per_s": (pairs_per_step(n) - q_skipped) / tq, "ms_per_step": 1e3 * tq,
+               "pairs_skipped_per_step": q_skipped, "h": resq["h"],
+               "note": "pair terms in Q32.32 fixed point on z-scored data; far tile pairs "
+                       "(every term exactly 0) are skipped and not counted"}
+
     batch = serve = evl = None
     if ws == 1 and not args.no_eval:
         evl = eval_leg(kde, torch, dev, stream, flush)
@@ -490,6 +514,8 @@ def run_ours(args, ws, rank, local):
     if fp64:
         line["fp64"] = fp64
         line["fp32_over_fp64"] = value / fp64["value"]
+    if q32:
+        line["q32"] = q32
     if batch:
         line["batch"] = batch
         if fp64:
@@ -525,6 +551,8 @@ def run_ours(args, ws, rank, local):
                 np.max(np.abs(evl["values"][pick] - ref_e) / ref_e))
         if fp64:
             line["accuracy"]["rel_err_fp64_vs_oracle"] = rel_errors(res64, ref)
+        if q32:
+            line["q32"]["rel_err_h_vs_fp64_oracle"] = abs(q32["h"] - ref["h"]) / ref["h"]
     print(json.dumps(line))
 
 

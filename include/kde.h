@@ -71,9 +71,16 @@ typedef enum {
  * is added to every difference as well.  Rounding only drops below the stated
  * accuracy for extreme R / g (e.g. clusters thousands of bandwidths apart),
  * where KDE_FP64 is the safer choice. */
+/* KDE_Q32 is the paper's arithmetic (Section 4.1): the data are z-scored
+ * (Eq. 3) and each pair term of Steps IV / VI is taken in Q32.32 fixed point
+ * (int64, 32 fractional bits, products truncated toward -inf, exp by a Remez
+ * polynomial), summed exactly; the scalar steps are binary64.  Its error on h
+ * is of the scale of the paper's Table 4.  r in {4, 6} only; not served by
+ * the continuous-batching server. */
 typedef enum {
     KDE_FP32 = 0,            /* binary32 pair terms, binary64 elsewhere */
-    KDE_FP64 = 1             /* binary64 everywhere */
+    KDE_FP64 = 1,            /* binary64 everywhere */
+    KDE_Q32 = 2              /* Q32.32 fixed-point pair terms on z-scored data */
 } kde_precision;
 
 /* Every scalar of Algorithm 1 for one sample.  In a device-memory output the

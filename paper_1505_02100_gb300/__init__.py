@@ -21,7 +21,7 @@ LIB_PATH = os.path.join(_HERE, "libkde.so")
 
 KDE_OK, KDE_ERR_INVALID, KDE_ERR_DEGENERATE, KDE_ERR_DOMAIN = 0, 1, 2, 3
 KDE_ERR_OOM, KDE_ERR_CUDA, KDE_ERR_TIMEOUT, KDE_ERR_BUSY = 4, 5, 6, 7
-KDE_FP32, KDE_FP64 = 0, 1
+KDE_FP32, KDE_FP64, KDE_Q32 = 0, 1, 2
 STATUS_NAMES = {0: "OK", 1: "INVALID", 2: "DEGENERATE", 3: "DOMAIN", 4: "OOM", 5: "CUDA",
                 6: "TIMEOUT", 7: "BUSY"}
 RESULT_FIELDS = ("mean", "sigma", "psi8", "g1", "psi6", "g2", "psi4", "h")

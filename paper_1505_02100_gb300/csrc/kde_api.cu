@@ -514,7 +514,7 @@ kde_status plugin_one(const void* x, int x_f32, int64_t n, kde_precision prec, k
                       void* stream) {
   if (!x || !out) return set_err(KDE_ERR_INVALID, "null pointer");
   if (n < 2) return set_err(KDE_ERR_INVALID, "n < 2");
-  if (prec != KDE_FP32 && prec != KDE_FP64) return set_err(KDE_ERR_INVALID, "bad precision");
+  if (prec != KDE_FP32 && prec != KDE_FP64 && prec != KDE_Q32) return set_err(KDE_ERR_INVALID, "bad precision");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   Workspace* W = nullptr;
   kde_status st = get_workspace(s, &W);
@@ -538,7 +538,8 @@ kde_status plugin_stages_one(const double* x, int64_t n, int stages, kde_precisi
   if (!x || !out) return set_err(KDE_ERR_INVALID, "null pointer");
   if (n < 2) return set_err(KDE_ERR_INVALID, "n < 2");
   if (stages < 1 || stages > 4) return set_err(KDE_ERR_INVALID, "stages must be 1..4");
-  if (prec != KDE_FP32 && prec != KDE_FP64) return set_err(KDE_ERR_INVALID, "bad precision");
+  if (prec != KDE_FP32 && prec != KDE_FP64 && prec != KDE_Q32) return set_err(KDE_ERR_INVALID, "bad precision");
+  if (prec == KDE_Q32 && stages > 2) return set_err(KDE_ERR_INVALID, "KDE_Q32 evaluates psi_4 and psi_6 only");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   Workspace* W = nullptr;
   kde_status st = get_workspace(s, &W);
@@ -563,7 +564,8 @@ kde_status psi_run(const double* x, int64_t n, int r, double g, kde_precision pr
   if (n < 2) return set_err(KDE_ERR_INVALID, "n < 2");
   if (r != 4 && r != 6 && r != 8 && r != 10) return set_err(KDE_ERR_INVALID, "r must be 4, 6, 8 or 10");
   if (!(g > 0) || !std::isfinite(g)) return set_err(KDE_ERR_INVALID, "g must be finite and > 0");
-  if (prec != KDE_FP32 && prec != KDE_FP64) return set_err(KDE_ERR_INVALID, "bad precision");
+  if (prec != KDE_FP32 && prec != KDE_FP64 && prec != KDE_Q32) return set_err(KDE_ERR_INVALID, "bad precision");
+  if (prec == KDE_Q32 && r > 6) return set_err(KDE_ERR_INVALID, "KDE_Q32 evaluates psi_4 and psi_6 only");
   kde_status st = get_workspace(s, Wout);
   if (st != KDE_OK) return st;
   build_plan(P, prec, r, 0, &n, 1, g);
@@ -636,7 +638,7 @@ kde_status kde_plugin_h_batch(const double* x_packed, const int64_t* offsets, in
                               kde_precision prec, kde_result* out, void* stream) {
   if (!x_packed || !offsets || !out) return set_err(KDE_ERR_INVALID, "null pointer");
   if (m < 1) return set_err(KDE_ERR_INVALID, "m < 1");
-  if (prec != KDE_FP32 && prec != KDE_FP64) return set_err(KDE_ERR_INVALID, "bad precision");
+  if (prec != KDE_FP32 && prec != KDE_FP64 && prec != KDE_Q32) return set_err(KDE_ERR_INVALID, "bad precision");
   if (offsets[0] != 0) return set_err(KDE_ERR_INVALID, "offsets[0] must be 0");
   std::vector<int64_t> ns(static_cast<size_t>(m));
   for (int64_t k = 0; k < m; ++k) {

@@ -51,6 +51,7 @@ constexpr int kFMin = 4, kFMax = 21;           // 2^(-6F) must stay a normal bin
 constexpr double kPadMargin = 1000.0;         // |u| >= 1000 against padding: the term vanishes
 constexpr double kFp32RangeLimit = 1.0e30;    // max|u| 2^F beyond this: not representable
 constexpr double kFp64RangeLimit = 1.0e45;
+constexpr double kQ32ZLimit = 536870912.0;      // Q32.32: |z| < 2^29 keeps differences in int64
 
 struct SampleDesc {
   int64_t x_off, n;

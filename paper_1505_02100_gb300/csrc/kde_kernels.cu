@@ -120,6 +120,22 @@ __device__ bool set_psi_scale(SampleState* st, double g, int prec) {
     st->scale = two_f / g;
     st->pad_lo = kYBias - P;
     st->pad_hi = kYBias + P;
+  } else if (prec == KDE_Q32) {
+    // z-scored values (Eq. 3); the kernel takes u = z-difference * (sigma / g)
+    const double sigma = st->res.sigma;
+    if (!(sigma > 0.0)) {
+      st->res.status = KDE_ERR_DEGENERATE;
+      return false;
+    }
+    const double zmax = fmax(st->xmax - st->res.mean, st->res.mean - st->xmin) / sigma;
+    if (!(zmax < kQ32ZLimit)) {
+      st->res.status = KDE_ERR_INVALID;
+      return false;
+    }
+    st->F = 0;
+    st->scale = sigma / g;
+    st->pad_hi = kQ32ZLimit + 1.0;   // z units: padding is never within 64 bandwidths
+    st->pad_lo = -st->pad_hi;
   } else {
     if (!(W < kFp64RangeLimit)) {
       st->res.status = KDE_ERR_INVALID;
@@ -160,9 +176,9 @@ __device__ __forceinline__ void record_psi(SampleState* st, int r, double psi, d
 }
 
 // Pilot bandwidth for psi_r from psi_{r+2} (Steps III and V, mu2 = 1); sets the
-// scale of the next pair launch.  false (DOMAIN) if the ratio is not positive.
-template <int PREC>
-__device__ bool next_pilot(SampleState* st, int r, double psi_up, double n) {
+// scale of the next pair launch for precision `prec`.  false (DOMAIN) if the
+// ratio is not positive.
+__device__ bool next_pilot(SampleState* st, int r, double psi_up, double n, int prec) {
   const double ratio = -2.0 * kernel_deriv_at_zero(r) / (psi_up * n);
   if (!(ratio > 0.0)) {
     st->res.status = KDE_ERR_DOMAIN;
@@ -172,7 +188,7 @@ __device__ bool next_pilot(SampleState* st, int r, double psi_up, double n) {
   st->sres.g[r / 2 - 2] = g;
   if (r == 6) st->res.g1 = g;
   if (r == 4) st->res.g2 = g;
-  return set_psi_scale(st, g, PREC);
+  return set_psi_scale(st, g, prec);
 }
 
 // ---------------------------------------------------------------------------
@@ -329,8 +345,7 @@ __global__ void __launch_bounds__(kMomThreads) moments_kernel(MomentsArgs a) {
     st->sres.psi[top / 2 - 2] = psi_ns;
     if (top == 8) st->res.psi8 = psi_ns;
     if (top == 6) st->res.psi6 = psi_ns;
-    if (d.prec == KDE_FP32) next_pilot<KDE_FP32>(st, top - 2, psi_ns, n);
-    else next_pilot<KDE_FP64>(st, top - 2, psi_ns, n);
+    next_pilot(st, top - 2, psi_ns, n, d.prec);
     return;
   }
   set_psi_scale(st, g, d.prec);
@@ -354,6 +369,12 @@ __global__ void __launch_bounds__(kPrescaleThreads) prescale_kernel(PrescaleArgs
   const SampleState& st = a.state[k];
   if (st.res.status != KDE_OK) return;
   const double z = __dmul_rn(__dsub_rn(load_x(a.x, a.x_is_f32, d.x_off + i), st.center), st.scale);
+  if (d.prec == KDE_Q32) {
+    // Eq. 3 in binary64, then truncated to Q32.32
+    const double zz = __ddiv_rn(__dsub_rn(load_x(a.x, a.x_is_f32, d.x_off + i), st.res.mean), st.res.sigma);
+    static_cast<long long*>(a.y)[d.y_off + i] = static_cast<long long>(floor(__dmul_rn(zz, 4294967296.0)));
+    return;
+  }
   if (d.prec == KDE_FP32) {
     // grid value and what rounding to it left over: hi + lo = kYBias + z to ~2^-24
     const float hi = static_cast<float>(kYBias + rint(z));
@@ -608,6 +629,9 @@ __device__ __forceinline__ void tri_index(int64_t p, int64_t nt, int64_t& I, int
   J = i + (p - S(i));
 }
 
+template <int PREC, int RORD>
+__device__ void finish_psi(const PairArgs& a, const SampleDesc& d, SampleState* st, double s);
+
 template <int PREC, int THREADS, int ROWS, int RORD>
 __device__ void finalize_pairs(const PairArgs& a, const SampleDesc& d, SampleState* st,
                                double* red) {
@@ -617,6 +641,13 @@ __device__ void finalize_pairs(const PairArgs& a, const SampleDesc& d, SampleSta
   if (threadIdx.x != 0) return;
   st->done_pairs = 0;
   if (st->res.status != KDE_OK) return;
+  finish_psi<PREC, RORD>(a, d, st, s);
+}
+
+// psi_r from the pair sum s = sum_{i<j} He_r(u) exp(-u^2/2) (Eqs. 6-7), then the
+// next step of the chain.  Thread 0 only.
+template <int PREC, int RORD>
+__device__ void finish_psi(const PairArgs& a, const SampleDesc& d, SampleState* st, double s) {
   const double n = static_cast<double>(d.n);
   const double g = st->g_cur;
   // Eqs. 6-7: [2 sum_{i<j} K^(r) + n K^(r)(0)] / (n^2 g^(r+1)), K^(r) = He_r phi
@@ -629,7 +660,7 @@ __device__ void finalize_pairs(const PairArgs& a, const SampleDesc& d, SampleSta
   }
   record_psi(st, RORD, psi, g);
   if (RORD > 4) {
-    next_pilot<PREC>(st, RORD - 2, psi, n);   // Steps V (and their continuation above)
+    next_pilot(st, RORD - 2, psi, n, PREC);   // Steps V (and their continuation above)
     return;
   }
   if (!(psi > 0.0)) {
@@ -807,6 +838,209 @@ __global__ void __launch_bounds__(THREADS, (pair_min_blocks<PREC, THREADS, ROWS,
   }
 }
 
+
+// ---------------------------------------------------------------------------
+// Q32.32 fixed point (Section 4.1): the paper's arithmetic for the pair terms
+// ---------------------------------------------------------------------------
+// int64 raw values, value = raw * 2^-32.  Products keep the high part of the
+// exact 128-bit product (truncation toward -inf).  z-scored data (Eq. 3),
+// u = (z_i - z_j) * (sigma / g), w = u^2, He_r(w) by Horner, exp(-w/2) as
+// 2^-t with t = w / (2 ln 2) = k + f, 2^-f by a degree-8 minimax polynomial
+// on [0, 1) (absolute error 0.002 of the last place; coefficients fitted by
+// our own Remez exchange), shifted right by k.  Sums are exact in int64 per
+// work item and int128 per sample, so the result does not depend on order.
+
+constexpr long long kQOne = 1LL << 32;
+constexpr long long kQInvTwoLn2 = 3098164009LL;   // round(2^32 / (2 ln 2))
+
+__device__ __forceinline__ long long qmul(long long a, long long b) {
+  const long long hi = __mul64hi(a, b);
+  const unsigned long long lo = static_cast<unsigned long long>(a) * static_cast<unsigned long long>(b);
+  return static_cast<long long>((static_cast<unsigned long long>(hi) << 32) | (lo >> 32));
+}
+
+// 2^32 exp(-w/2) for the Q32.32 value w >= 0
+__device__ __forceinline__ long long q_exp_half(long long w) {
+  const long long t = qmul(w, kQInvTwoLn2);
+  const long long k = t >> 32;
+  if (k >= 63) return 0;
+  const long long f = t & 0xffffffffLL;
+  long long q = 4028LL;
+  q = qmul(q, f) - 62610LL;
+  q = qmul(q, f) + 658738LL;
+  q = qmul(q, f) - 5725081LL;
+  q = qmul(q, f) + 41308991LL;
+  q = qmul(q, f) - 238388224LL;
+  q = qmul(q, f) + 1031764981LL;
+  q = qmul(q, f) - 2977044471LL;
+  q = qmul(q, f) + 4294967296LL;
+  return q >> k;
+}
+
+// He_r(u) exp(-u^2/2) in Q32.32 for the z-difference d; 0 where the truncated
+// exponential is 0 anyway (|u| >= 64 or u^2 >= 45)
+template <int RORD>
+__device__ __forceinline__ long long q_term(long long d, long long ginv, double ginv_d) {
+  if (fabs(static_cast<double>(d) * ginv_d) >= 64.0 * 18446744073709551616.0) return 0;
+  const long long u = qmul(d, ginv);
+  const long long w = qmul(u, u);
+  if (w >= 45 * kQOne) return 0;
+  long long p;
+  if (RORD == 6) {
+    p = qmul(w - 15 * kQOne, w) + 45 * kQOne;
+    p = qmul(p, w) - 15 * kQOne;
+  } else {
+    p = qmul(w - 6 * kQOne, w) + 3 * kQOne;
+  }
+  return qmul(p, q_exp_half(w));
+}
+
+template <int THREADS>
+__device__ long long block_sum_i64(long long v, long long* red) {
+  red[threadIdx.x] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    long long t = 0;
+    for (int i = 0; i < THREADS; ++i) t += red[i];
+    red[0] = t;
+  }
+  __syncthreads();
+  const long long r = red[0];
+  __syncthreads();
+  return r;
+}
+
+template <int THREADS, int RORD>
+__device__ void finalize_q32(const PairArgs& a, const SampleDesc& d, SampleState* st, __int128* red) {
+  __int128 s = 0;
+  for (int64_t i = threadIdx.x; i < d.nchunks; i += THREADS)
+    s += static_cast<__int128>(__double_as_longlong(__ldcg(a.slots + d.slot_off + i)));
+  red[threadIdx.x] = s;
+  __syncthreads();
+  if (threadIdx.x != 0) return;
+  __int128 t = 0;
+  for (int i = 0; i < THREADS; ++i) t += red[i];
+  st->done_pairs = 0;
+  if (st->res.status != KDE_OK) return;
+  const long long hi = static_cast<long long>(t >> 64);
+  const unsigned long long lo = static_cast<unsigned long long>(t);
+  const double sum = (static_cast<double>(hi) * 18446744073709551616.0 + static_cast<double>(lo)) / 4294967296.0;
+  finish_psi<KDE_Q32, RORD>(a, d, st, sum);
+}
+
+template <int THREADS, int ROWS, int RORD>
+__global__ void __launch_bounds__(THREADS) pairs_q32_kernel(PairArgs a) {
+  constexpr int TILE = THREADS * ROWS;
+  __shared__ long long tile[TILE];
+  __shared__ __int128 red[THREADS];
+  __shared__ long long s_item;
+  __shared__ int s_last;
+  long long* red64 = reinterpret_cast<long long*>(red);
+  const int tid = threadIdx.x;
+  for (;;) {
+    if (tid == 0) s_item = static_cast<long long>(atomicAdd(a.counters, 1ull));
+    __syncthreads();
+    const long long item = s_item;
+    if (item >= a.n_items) break;
+    const uint64_t wi = a.items[item];
+    const int64_t k = static_cast<int64_t>(wi >> 32);
+    const int64_t c = static_cast<int64_t>(wi & 0xffffffffull);
+    const SampleDesc d = a.desc[k];
+    SampleState* st = a.state + k;
+    long long acc_off = 0, acc_diag = 0;
+    int64_t diag_units = 0, skipped_pairs = 0;
+    if (st->res.status == KDE_OK) {
+      const long long* __restrict__ y = static_cast<const long long*>(a.y) + d.y_off;
+      const long long pad_lo = static_cast<long long>(floor(st->pad_lo * 4294967296.0));
+      const long long pad_hi = static_cast<long long>(floor(st->pad_hi * 4294967296.0));
+      const long long ginv = static_cast<long long>(floor(st->scale * 4294967296.0));
+      const double ginv_d = static_cast<double>(ginv);
+      int64_t p = c * d.chunk;
+      const int64_t pend = (p + d.chunk < d.ntp) ? p + d.chunk : d.ntp;
+      int64_t I, J;
+      tri_index(p, d.nt, I, J);
+      long long w[ROWS];
+      auto load_rows = [&](int64_t I_) {
+#pragma unroll
+        for (int r = 0; r < ROWS; ++r) {
+          const int64_t i = I_ * TILE + static_cast<int64_t>(tid) * ROWS + r;
+          w[r] = i < d.n ? y[i] : pad_lo;
+        }
+      };
+      load_rows(I);
+      for (; p < pend; ++p) {
+        bool far = false;
+        if (J > I) {   // sorted: smallest distance = first column - last row; u >= 6.8 gives 0
+          const double gap = static_cast<double>(y[J * TILE] - y[I * TILE + TILE - 1]) * ginv_d *
+                             (1.0 / 18446744073709551616.0);
+          far = gap >= 6.8;
+        }
+        if (far) {
+          const int64_t cols = d.n - J * TILE;
+          skipped_pairs += static_cast<int64_t>(TILE) * (cols < TILE ? cols : TILE);
+        } else {
+          __syncthreads();
+#pragma unroll
+          for (int r = 0; r < ROWS; ++r) {
+            const int64_t j = J * TILE + tid + r * THREADS;
+            tile[tid + r * THREADS] = j < d.n ? y[j] : pad_hi;
+          }
+          __syncthreads();
+          long long acc = 0;
+#pragma unroll 2
+          for (int jj = 0; jj < TILE; ++jj) {
+            const long long b = tile[jj];
+#pragma unroll
+            for (int r = 0; r < ROWS; ++r) {
+              const long long dz = w[r] - b;   // the term is even: take |dz| (truncation is not odd)
+              acc += q_term<RORD>(dz < 0 ? -dz : dz, ginv, ginv_d);
+            }
+          }
+          if (I == J) {   // full square: symmetric pairs twice, the diagonal once
+            acc_diag += acc;
+            const int64_t valid = d.n - I * TILE;
+            diag_units += valid < TILE ? valid : TILE;
+          } else {
+            acc_off += acc;
+          }
+        }
+        if (++J == d.nt) {
+          ++I;
+          J = I;
+          if (p + 1 < pend) load_rows(I);
+        }
+      }
+      if (tid == 0 && skipped_pairs > 0)
+        atomicAdd(&st->skipped[RORD == 6 ? 0 : 1], static_cast<unsigned long long>(skipped_pairs));
+    }
+    const long long off = block_sum_i64<THREADS>(acc_off, red64);
+    const long long dg = block_sum_i64<THREADS>(acc_diag, red64);
+    if (tid == 0) {
+      // the diagonal terms are exactly He_r(0) (u = 0, exp = 1); the rest of a
+      // diagonal tile holds each unordered pair twice
+      const long long he0 = static_cast<long long>(he_at_zero<RORD>()) * kQOne;
+      const long long item_sum = off + (dg - diag_units * he0) / 2;
+      a.slots[d.slot_off + c] = __longlong_as_double(item_sum);
+      __threadfence();
+      const unsigned prev = atomicAdd(&st->done_pairs, 1u);
+      s_last = (prev + 1 == static_cast<unsigned>(d.nchunks));
+    }
+    __syncthreads();
+    if (s_last) {
+      __threadfence();
+      finalize_q32<THREADS, RORD>(a, d, st, red);
+    }
+    __syncthreads();
+  }
+  if (tid == 0) {
+    const unsigned long long e = atomicAdd(a.counters + 1, 1ull);
+    if (e + 1 == gridDim.x) {
+      a.counters[0] = 0ull;
+      a.counters[1] = 0ull;
+    }
+  }
+}
+
 // ---------------------------------------------------------------------------
 // configuration table
 // ---------------------------------------------------------------------------
@@ -835,23 +1069,27 @@ const ConfigEntry kFp64Configs[] = {
     KDE_CFG(KDE_FP64, 64, 4, 4),    // T = 256
 };
 #undef KDE_CFG
+const ConfigEntry kQ32Configs[] = {
+    {{128, 2}, pairs_q32_kernel<128, 2, 4>, pairs_q32_kernel<128, 2, 6>, nullptr, nullptr},   // T = 256
+};
 
 const ConfigEntry& entry(int prec, int cfg) {
-  return prec == KDE_FP32 ? kFp32Configs[cfg] : kFp64Configs[cfg];
+  return prec == KDE_FP32 ? kFp32Configs[cfg] : prec == KDE_Q32 ? kQ32Configs[cfg] : kFp64Configs[cfg];
 }
 
 }  // namespace
 
 int pair_config_count(int prec) {
-  return prec == KDE_FP32 ? static_cast<int>(sizeof(kFp32Configs) / sizeof(kFp32Configs[0]))
-                          : static_cast<int>(sizeof(kFp64Configs) / sizeof(kFp64Configs[0]));
+  return prec == KDE_FP32  ? static_cast<int>(sizeof(kFp32Configs) / sizeof(kFp32Configs[0]))
+         : prec == KDE_Q32 ? static_cast<int>(sizeof(kQ32Configs) / sizeof(kQ32Configs[0]))
+                           : static_cast<int>(sizeof(kFp64Configs) / sizeof(kFp64Configs[0]));
 }
 
 PairConfig pair_config(int prec, int cfg) { return entry(prec, cfg).cfg; }
 
 int pair_blocks_per_sm(int prec, int cfg) {
-  static int cache[2][8] = {};
-  int& v = cache[prec == KDE_FP32 ? 0 : 1][cfg];
+  static int cache[3][8] = {};
+  int& v = cache[prec][cfg];
   if (v == 0) {
     const ConfigEntry& e = entry(prec, cfg);
     int b4 = 0, b6 = 0;
@@ -894,8 +1132,8 @@ cudaError_t launch_pairs(int prec, int cfg, const PairArgs& a, int grid, cudaStr
   const ConfigEntry& e = entry(prec, cfg);
   PairKernel k = a.r == 6 ? e.k6 : a.r == 8 ? e.k8 : a.r == 10 ? e.k10 : e.k4;
   if (a.r >= 8) {   // the higher orders may hold more registers: at most their resident count
-    static int cache[2][8][2] = {};
-    int& v = cache[prec == KDE_FP32 ? 0 : 1][cfg][a.r == 8 ? 0 : 1];
+    static int cache[3][8][2] = {};
+    int& v = cache[prec][cfg][a.r == 8 ? 0 : 1];
     if (v == 0) {
       cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, k, e.cfg.threads, 0);
       if (v < 1) v = 1;

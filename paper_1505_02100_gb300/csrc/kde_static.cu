@@ -116,7 +116,8 @@ extern "C" kde_status kde_psi_static(const double* x, int64_t n, int r, double g
                                         " values; use kde_psi");
   if (r != 4 && r != 6 && r != 8 && r != 10) return set_err(KDE_ERR_INVALID, "r must be 4, 6, 8 or 10");
   if (!(g > 0) || !std::isfinite(g)) return set_err(KDE_ERR_INVALID, "g must be finite and > 0");
-  if (prec != KDE_FP32 && prec != KDE_FP64) return set_err(KDE_ERR_INVALID, "bad precision");
+  if (prec != KDE_FP32 && prec != KDE_FP64 && prec != KDE_Q32) return set_err(KDE_ERR_INVALID, "bad precision");
+  if (prec == KDE_Q32 && r > 6) return set_err(KDE_ERR_INVALID, "KDE_Q32 evaluates psi_4 and psi_6 only");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   unsigned char* base = nullptr;
   kde_status st = scratch_for_current_device(&base);

@@ -34,7 +34,7 @@ constexpr int kTuneDevices = 64;
 constexpr float kTuneMargin = 0.03f;   // another configuration must be >= 3% faster
 
 std::mutex g_tune_mu;
-int g_tuned[kTuneDevices][2][kTuneBuckets];   // -1: not tuned
+int g_tuned[kTuneDevices][3][kTuneBuckets];   // -1: not tuned
 bool g_tuned_init = false;
 
 void init_table_locked() {
@@ -82,7 +82,7 @@ int tuned_config(int prec, int64_t n) {
   }
   std::lock_guard<std::mutex> lk(g_tune_mu);
   init_table_locked();
-  return g_tuned[dev][prec == KDE_FP32 ? 0 : 1][bucket_of(n)];
+  return g_tuned[dev][prec][bucket_of(n)];
 }
 
 }  // namespace kde
@@ -90,7 +90,7 @@ int tuned_config(int prec, int64_t n) {
 using namespace kde;
 
 extern "C" kde_status kde_autotune(kde_precision prec, int32_t* chosen, int cap) {
-  if (prec != KDE_FP32 && prec != KDE_FP64) return set_err(KDE_ERR_INVALID, "bad precision");
+  if (prec != KDE_FP32 && prec != KDE_FP64 && prec != KDE_Q32) return set_err(KDE_ERR_INVALID, "bad precision");
   if (chosen && cap < kTuneBuckets) return set_err(KDE_ERR_INVALID, "need room for 5 configurations");
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kTuneDevices) {
@@ -152,7 +152,7 @@ extern "C" kde_status kde_autotune(kde_precision prec, int32_t* chosen, int cap)
       std::lock_guard<std::mutex> lk(g_tune_mu);
       init_table_locked();
       for (int b = 0; b < kTuneBuckets; ++b) {
-        g_tuned[dev][prec == KDE_FP32 ? 0 : 1][b] = best_cfg[b];
+        g_tuned[dev][prec][b] = best_cfg[b];
         if (chosen) chosen[b] = best_cfg[b];
       }
     }
@@ -170,7 +170,7 @@ extern "C" kde_status kde_autotune(kde_precision prec, int32_t* chosen, int cap)
 }
 
 extern "C" kde_status kde_autotune_clear(kde_precision prec) {
-  if (prec != KDE_FP32 && prec != KDE_FP64) return set_err(KDE_ERR_INVALID, "bad precision");
+  if (prec != KDE_FP32 && prec != KDE_FP64 && prec != KDE_Q32) return set_err(KDE_ERR_INVALID, "bad precision");
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kTuneDevices) {
     cudaGetLastError();
@@ -178,13 +178,13 @@ extern "C" kde_status kde_autotune_clear(kde_precision prec) {
   }
   std::lock_guard<std::mutex> lk(g_tune_mu);
   init_table_locked();
-  for (int& c : g_tuned[dev][prec == KDE_FP32 ? 0 : 1]) c = -1;
+  for (int& c : g_tuned[dev][prec]) c = -1;
   return KDE_OK;
 }
 
 extern "C" kde_status kde_tile_config(kde_precision prec, int64_t n, int32_t* info) {
   if (!info) return set_err(KDE_ERR_INVALID, "null pointer");
-  if (prec != KDE_FP32 && prec != KDE_FP64) return set_err(KDE_ERR_INVALID, "bad precision");
+  if (prec != KDE_FP32 && prec != KDE_FP64 && prec != KDE_Q32) return set_err(KDE_ERR_INVALID, "bad precision");
   if (n < 2) return set_err(KDE_ERR_INVALID, "n < 2");
   const int cfg = choose_config(prec, n);
   const PairConfig pc = pair_config(prec, cfg);
