@@ -33,6 +33,7 @@ import re
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
@@ -113,7 +114,8 @@ class ClockSampler:
     def __init__(self, gpu: int):
         self.gpu = gpu
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_gpu{gpu}.csv")
+        self.path = os.path.join(os.environ.get("KDE_BENCH_CLOCKS_DIR", tempfile.gettempdir()),
+                                 f"kde_bench_clocks_gpu{gpu}_{os.getpid()}.csv")
 
     def __enter__(self):
         try:
