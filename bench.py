@@ -183,13 +183,13 @@ def measured_traffic(tile_config: int):
         text = open(TRAFFIC_FILE).read()
     except OSError:
         return None
-    fields = dict(re.findall(r"^- (kernel_source_sha256|dram_bytes_per_launch|tile_config): `([^`]+)`",
+    fields = dict(re.findall(r"^- (kernel_source_sha256|dram_bytes_per_launch_cfg\d+): `([^`]+)`",
                              text, re.M))
     digest = hashlib.sha256(open(KERNEL_SOURCE, "rb").read()).hexdigest()
-    if (fields.get("kernel_source_sha256") != digest or "dram_bytes_per_launch" not in fields
-            or fields.get("tile_config") != str(tile_config)):
+    key = f"dram_bytes_per_launch_cfg{tile_config}"
+    if fields.get("kernel_source_sha256") != digest or key not in fields:
         return None
-    return float(fields["dram_bytes_per_launch"])
+    return float(fields[key])
 
 
 def alu_peak(r: int, sms: int, f_mhz: float):
