@@ -377,8 +377,10 @@ __global__ void __launch_bounds__(kPrescaleThreads) prescale_kernel(PrescaleArgs
   }
   if (d.prec == KDE_FP32) {
     // grid value and what rounding to it left over: hi + lo = kYBias + z to ~2^-24
-    const float hi = static_cast<float>(kYBias + rint(z));
-    const float lo = static_cast<float>((kYBias + z) - static_cast<double>(hi));
+    // the grid scaled by 2^-F (exact): differences come out in u-units
+    const float hi_grid = static_cast<float>(kYBias + rint(z));
+    const float hi = ldexpf(hi_grid, -st.F);
+    const float lo = static_cast<float>(ldexp((kYBias + z) - static_cast<double>(hi_grid), -st.F));
     static_cast<float2*>(a.y)[d.y_off + i] = make_float2(hi, lo);
   } else {
     static_cast<double*>(a.y)[d.y_off + i] = z;
@@ -452,13 +454,13 @@ __host__ __device__ constexpr double he_at_zero() {
 }
 
 // exp(-u^2/2) in binary32 on the FMA pipe, as 2^t with t = -u^2 / (2 ln 2).
-// In grid units t = -v c with c = 2^(-2F) / (2 ln 2) = c_hi + c_lo split into
-// two binary32 values.  k = round(v c_hi) by the 1.5 * 2^23 rounding trick,
-// f = k - v c_hi in [-1/2, 1/2] from one FFMA (the exact value of a 48-bit
-// product minus an integer, rounded once), 2^f by a degree-8 minimax
-// polynomial (relative error 1.1e-12, fitted by Remez exchange, p(0) = 1
-// exactly), and k goes straight into the exponent field.  That is
-// exp(-u^2/2) scaled by 2^(-v c_lo) = 1 - v c_lo ln 2 + O(1e-12).
+// With w = u^2 (the values are stored in u-units), t = -w c with c = 1 / (2 ln 2)
+// = kCHi + c_lo split into two binary32 values.  k = round(w kCHi) by the
+// 1.5 * 2^23 rounding trick, f = k - w kCHi in [-1/2, 1/2] from one FFMA (the
+// exact value of a 48-bit product minus an integer, rounded once), 2^f by a
+// degree-8 minimax polynomial (relative error 1.1e-12, fitted by Remez
+// exchange, p(0) = 1 exactly), and k goes straight into the exponent field.
+// That is exp(-u^2/2) scaled by 2^(-w c_lo) = 1 - w c_lo ln 2 + O(1e-12).
 //
 // The c_lo factor is not applied to f or to the term: there it would be a
 // smooth correction a few units in the last place, added to a value already
@@ -479,10 +481,15 @@ __host__ __device__ constexpr double he_at_zero() {
 // (t - k ln2_hi with t large) ~8e-6 on psi6.
 // u^2 is clamped to 125 * 2 ln 2 (~173): beyond it every term is below 1e-31,
 // the exponent stays normal and He_r stays finite.  Tile pairs whose largest
-// distance is below the clamp skip it (CLAMP = false).
+// distance is below the clamp skip it (CLAMP = false).  Since every scaling by
+// 2^-F is exact, these terms are bit for bit those of the grid units.
 constexpr float kRoundMagic = 12582912.0f;                 // 1.5 * 2^23
 constexpr double kInvTwoLn2 = 0.72134752044448170367996234050095;
 constexpr float kMinT = 125.0f;
+// The binary32 pair terms work in u-units (w = u^2): c = 1 / (2 ln 2) = kCHi + c_lo
+constexpr float kCHi = static_cast<float>(kInvTwoLn2);
+constexpr double kCLoLn2 = (kInvTwoLn2 - static_cast<double>(kCHi)) * 0.69314718055994530942;
+constexpr float kWMax = kMinT / kCHi;   // u^2 clamp (~173)
 
 __device__ __forceinline__ float exp2_reduced(float f) {
   float q = 1.3344183e-06f;
@@ -496,19 +503,27 @@ __device__ __forceinline__ float exp2_reduced(float f) {
   return __fmaf_rn(q, f, 1.0f);
 }
 
-// One pair term, binary32, without its 2^(-v c_lo) factor: d = y_i - y_j in grid
-// units; c_hi = 2^(-2F) / (2 ln 2) rounded; vmax = kMinT / c_hi.
-// `vout` receives v: the term is too large by the relative amount v c_lo ln 2.
+// One pair term, binary32, without its 2^(-w c_lo) factor: d = u = y_i - y_j
+// (exact on the grid, in u-units).  The constants are compile-time immediates:
+// Hermite coefficients are the integers of Steps IV / VI (and their
+// continuation for r = 8, 10); a diagonal tile pair halves its sum afterwards.
+// `wout` receives w = u^2: the term is too large by the relative amount w c_lo ln 2.
 template <int RORD, bool CLAMP>
-__device__ __forceinline__ float term32(float d, const Coef<float, RORD>& cf, float c_hi, float vmax,
-                                        float p2f, float& vout) {
-  const float v = CLAMP ? fminf(__fmul_rn(d, d), vmax) : __fmul_rn(d, d);
-  const float yb = __fmaf_rn(v, -c_hi, kRoundMagic);      // low bits: k = round(t)
+__device__ __forceinline__ float term32(float d, float& wout) {
+  const float w = CLAMP ? fminf(__fmul_rn(d, d), kWMax) : __fmul_rn(d, d);   // u^2
+  const float yb = __fmaf_rn(w, -kCHi, kRoundMagic);      // low bits: k = round(t)
   const float kf = __fsub_rn(yb, kRoundMagic);
-  const float f = __fmaf_rn(v, -c_hi, -kf);               // t - k (c_hi part)
+  const float f = __fmaf_rn(w, -kCHi, -kf);               // t - k (c_hi part)
   const float e = __int_as_float(__float_as_int(exp2_reduced(f)) + (__float_as_int(yb) << 23));
-  const float p = Coef<float, RORD>::kOnW ? cf.horner(__fmul_rn(v, p2f)) : cf.horner(v);
-  vout = v;
+  float p;
+  if (RORD == 4) p = __fmaf_rn(__fadd_rn(w, -6.0f), w, 3.0f);
+  else if (RORD == 6) p = __fmaf_rn(__fmaf_rn(__fadd_rn(w, -15.0f), w, 45.0f), w, -15.0f);
+  else if (RORD == 8)
+    p = __fmaf_rn(__fmaf_rn(__fmaf_rn(__fadd_rn(w, -28.0f), w, 210.0f), w, -420.0f), w, 105.0f);
+  else
+    p = __fmaf_rn(__fmaf_rn(__fmaf_rn(__fmaf_rn(__fadd_rn(w, -45.0f), w, 630.0f), w, -3150.0f), w, 4725.0f),
+                  w, -945.0f);
+  wout = w;
   return __fmul_rn(p, e);
 }
 
@@ -545,9 +560,8 @@ struct Kahan32 {
 // (see term32), which goes to the thread's binary64 total `cacc`.
 template <int RORD, int ROWS, int CJ, int TILE, bool CLAMP, bool LO>
 __device__ __forceinline__ void tile_pass(const float* __restrict__ tile, const float* __restrict__ tile_lo,
-                                          const float (&w)[ROWS], const float (&wl)[ROWS],
-                                          const Coef<float, RORD>& cf, float c_hi, double c_lo_ln2,
-                                          float vmax, float p2f, Kahan32& acc, double& cacc) {
+                                          const float (&w)[ROWS], const float (&wl)[ROWS], float half,
+                                          Kahan32& acc, double& cacc) {
   static_assert(CJ == 4, "one float4 of columns per group of terms");
   float sum[ROWS], comp[ROWS], tv[ROWS];
 #pragma unroll
@@ -572,7 +586,7 @@ __device__ __forceinline__ void tile_pass(const float* __restrict__ tile, const 
         float v;
         // grid difference (exact), plus the residuals when the grid is coarse
         const float d = LO ? __fadd_rn(__fsub_rn(w[r], b[q]), __fsub_rn(wl[r], bl[q])) : __fsub_rn(w[r], b[q]);
-        t[q] = term32<RORD, CLAMP>(d, cf, c_hi, vmax, p2f, v);
+        t[q] = term32<RORD, CLAMP>(d, v);
         tv[r] = __fmaf_rn(t[q], v, tv[r]);
       }
       const float g4 = __fadd_rn(__fadd_rn(t[0], t[1]), __fadd_rn(t[2], t[3]));
@@ -585,10 +599,10 @@ __device__ __forceinline__ void tile_pass(const float* __restrict__ tile, const 
   float tvsum = 0.0f;
 #pragma unroll
   for (int r = 0; r < ROWS; ++r) {
-    acc.add(__fsub_rn(sum[r], comp[r]));
+    acc.add(__fmul_rn(half, __fsub_rn(sum[r], comp[r])));   // half = 1/2 on a diagonal tile: exact
     tvsum = __fadd_rn(tvsum, tv[r]);
   }
-  cacc -= static_cast<double>(tvsum) * c_lo_ln2;
+  cacc -= static_cast<double>(tvsum) * static_cast<double>(half) * kCLoLn2;
 }
 
 // One tile pair, FP64 (plain binary64 accumulation, accurate exp).
@@ -713,15 +727,12 @@ __global__ void __launch_bounds__(THREADS, (pair_min_blocks<PREC, THREADS, ROWS,
     if (st->res.status == KDE_OK) {
       using Y = typename Arith<PREC>::Y;
       const Y* __restrict__ y = static_cast<const Y*>(a.y) + d.y_off;
-      const T pad_lo = static_cast<T>(st->pad_lo), pad_hi = static_cast<T>(st->pad_hi);
-      const double p2 = ldexp(1.0, -2 * st->F);
-      const float c_hi = static_cast<float>(kInvTwoLn2 * p2);
-      const double c_lo_ln2 = (kInvTwoLn2 * p2 - static_cast<double>(c_hi)) * 0.69314718055994530942;
-      const float vmax = kMinT / c_hi;
-      const float p2f = static_cast<float>(p2);
-      Coef<T, RORD> full, half;
-      full.set(1.0, p2);
-      half.set(0.5, p2);
+      // binary32: grid values were stored in u-units (scaled by 2^-F); the pads too
+      const double unit = PREC == KDE_FP32 ? ldexp(1.0, -st->F) : 1.0;
+      const T pad_lo = static_cast<T>(st->pad_lo * unit), pad_hi = static_cast<T>(st->pad_hi * unit);
+      Coef<T, RORD> full, half;   // binary64 terms (u-units)
+      full.set(1.0, 1.0);
+      half.set(0.5, 1.0);
       int64_t p = c * d.chunk;
       const int64_t pend = (p + d.chunk < d.ntp) ? p + d.chunk : d.ntp;
       int64_t I, J;
@@ -744,7 +755,7 @@ __global__ void __launch_bounds__(THREADS, (pair_min_blocks<PREC, THREADS, ROWS,
         }
       };
       const bool lo_path = PREC == KDE_FP32 && st->F < kFLo;
-      const double margin = PREC == KDE_FP32 ? 1.0 : 0.0;   // |residual differences| <= 1 grid unit
+      const double margin = PREC == KDE_FP32 ? unit : 0.0;   // |residual differences| <= 1 grid unit
       load_rows(I);
       Kahan32 acc32;
       double cacc = 0.0;
@@ -753,7 +764,7 @@ __global__ void __launch_bounds__(THREADS, (pair_min_blocks<PREC, THREADS, ROWS,
       // of an off-diagonal tile pair is its first column minus its last row.  Beyond
       // the binary32 clamp every term is below 1e-31; beyond 40 bandwidths every
       // binary64 term underflows to exactly 0.
-      const double far2 = (PREC == KDE_FP32) ? static_cast<double>(vmax) : 1600.0;
+      const double far2 = (PREC == KDE_FP32) ? static_cast<double>(kWMax) : 1600.0;
       int64_t skipped_pairs = 0;
       for (; p < pend; ++p) {
         bool far = false;
@@ -789,13 +800,14 @@ __global__ void __launch_bounds__(THREADS, (pair_min_blocks<PREC, THREADS, ROWS,
           // The sample is sorted, so the largest |y_i - y_j| of the tile pair is
           // its last column minus its first row; tiles with padding always clamp.
           const double span = static_cast<double>(tile[TILE - 1]) - static_cast<double>(hi_of(y[I * TILE])) + margin;
-          const bool near = (J + 1) * TILE <= d.n && span * span <= static_cast<double>(vmax);
+          const bool near = (J + 1) * TILE <= d.n && span * span <= static_cast<double>(kWMax);
+          const float hf = diag ? 0.5f : 1.0f;
           if (lo_path) {
-            if (near) tile_pass<RORD, ROWS, CJ, TILE, false, true>(tile, tile_lo, w, wl, cf, c_hi, c_lo_ln2, vmax, p2f, acc32, cacc);
-            else tile_pass<RORD, ROWS, CJ, TILE, true, true>(tile, tile_lo, w, wl, cf, c_hi, c_lo_ln2, vmax, p2f, acc32, cacc);
+            if (near) tile_pass<RORD, ROWS, CJ, TILE, false, true>(tile, tile_lo, w, wl, hf, acc32, cacc);
+            else tile_pass<RORD, ROWS, CJ, TILE, true, true>(tile, tile_lo, w, wl, hf, acc32, cacc);
           } else {
-            if (near) tile_pass<RORD, ROWS, CJ, TILE, false, false>(tile, tile_lo, w, wl, cf, c_hi, c_lo_ln2, vmax, p2f, acc32, cacc);
-            else tile_pass<RORD, ROWS, CJ, TILE, true, false>(tile, tile_lo, w, wl, cf, c_hi, c_lo_ln2, vmax, p2f, acc32, cacc);
+            if (near) tile_pass<RORD, ROWS, CJ, TILE, false, false>(tile, tile_lo, w, wl, hf, acc32, cacc);
+            else tile_pass<RORD, ROWS, CJ, TILE, true, false>(tile, tile_lo, w, wl, hf, acc32, cacc);
           }
         } else {
           tile_pass64<RORD, ROWS, TILE>(tile, w, cf, acc64);
