@@ -158,16 +158,16 @@ class ClockSampler:
 
 # Instructions per pair of the binary32 pair kernel on a tile pair that needs
 # no clamp (all issue on the FP32/INT pipes, no MUFU):
-#   FADD  d = y_i - y_j (exact on the per-sample grid) ;  FMUL  v = d^2
-#   FFMA + FADD + FFMA   k = round(t), f = t - k for t = -v c_hi
+#   FADD  u = y_i - y_j (exact on the per-sample grid) ;  FMUL  w = u^2
+#   FFMA + FADD + FFMA   k = round(t), f = t - k for t = -w c_hi
 #   8 FFMA   degree-8 polynomial for 2^f
 #   SHL + IADD   2^k into the exponent field
-#   r/2 FFMA   Horner for He_r on v (3 for He_6, 2 for He_4)
-#   FMUL   term ;  FFMA   sum of term * v for the c_lo correction
-#   3/4 FADD + 4/4 FADD   groups of 4 terms, one Kahan step per group
+#   FADD + (r/2 - 1) FFMA   Horner for He_r on w, integer coefficients as immediates
+#   FMUL   term ;  FFMA   sum of term * w for the c_lo correction
+#   7/8 FADD + 4/8 FADD   groups of 8 terms, one Kahan step per group
 # Tile pairs that reach the clamp add one FMNMX.  The bound below uses the
 # smaller count, so it is the higher (stricter) roofline.
-ISSUE_PER_PAIR = {6: 21.75, 4: 20.75}
+ISSUE_PER_PAIR = {6: 21.375, 4: 20.375}
 KERNEL_SOURCE = os.path.join(os.path.dirname(os.path.abspath(__file__)),
                              "paper_1505_02100_gb300", "csrc", "kde_kernels.cu")
 TRAFFIC_FILE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "profiles",

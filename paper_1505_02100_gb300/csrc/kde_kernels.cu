@@ -551,8 +551,8 @@ struct Kahan32 {
 };
 
 // One tile pair, FP32: this thread's ROWS rows against the TILE columns in
-// shared memory.  Per row, each group of 4 terms (one float4 of columns) is
-// summed as a tree and added to the row's Kahan-compensated sum; the row sums
+// shared memory.  Per row, each group of CJ terms (CJ / 4 float4s of columns)
+// is summed as a tree and added to the row's Kahan-compensated sum; the row sums
 // are folded into the thread's running Kahan sum once per tile pair.  Sorted
 // tiles make the terms one accumulator sees nearly equal; plain binary32
 // summation of such runs drifts systematically, which the cancellation of the
@@ -562,7 +562,7 @@ template <int RORD, int ROWS, int CJ, int TILE, bool CLAMP, bool LO>
 __device__ __forceinline__ void tile_pass(const float* __restrict__ tile, const float* __restrict__ tile_lo,
                                           const float (&w)[ROWS], const float (&wl)[ROWS], float half,
                                           Kahan32& acc, double& cacc) {
-  static_assert(CJ == 4, "one float4 of columns per group of terms");
+  static_assert(CJ == 4 || CJ == 8, "one or two float4s of columns per group of terms");
   float sum[ROWS], comp[ROWS], tv[ROWS];
 #pragma unroll
   for (int r = 0; r < ROWS; ++r) sum[r] = comp[r] = tv[r] = 0.0f;
@@ -589,8 +589,9 @@ __device__ __forceinline__ void tile_pass(const float* __restrict__ tile, const 
         t[q] = term32<RORD, CLAMP>(d, v);
         tv[r] = __fmaf_rn(t[q], v, tv[r]);
       }
-      const float g4 = __fadd_rn(__fadd_rn(t[0], t[1]), __fadd_rn(t[2], t[3]));
-      const float y = __fsub_rn(g4, comp[r]);
+      float g = __fadd_rn(__fadd_rn(t[0], t[1]), __fadd_rn(t[2], t[3]));
+      if (CJ == 8) g = __fadd_rn(g, __fadd_rn(__fadd_rn(t[CJ / 2], t[CJ / 2 + 1]), __fadd_rn(t[CJ / 2 + 2], t[CJ / 2 + 3])));
+      const float y = __fsub_rn(g, comp[r]);
       const float tt = __fadd_rn(sum[r], y);
       comp[r] = __fsub_rn(__fsub_rn(tt, sum[r]), y);
       sum[r] = tt;
@@ -1069,11 +1070,11 @@ struct ConfigEntry {
     pairs_kernel<P, TH, RW, CJ, 8>, pairs_kernel<P, TH, RW, CJ, 10> }
 
 const ConfigEntry kFp32Configs[] = {
-    KDE_CFG(KDE_FP32, 128, 4, 4),   // T = 512
-    KDE_CFG(KDE_FP32, 64, 8, 4),    // T = 512
-    KDE_CFG(KDE_FP32, 256, 4, 4),   // T = 1024
-    KDE_CFG(KDE_FP32, 64, 4, 4),    // T = 256
-    KDE_CFG(KDE_FP32, 128, 2, 4),   // T = 256
+    KDE_CFG(KDE_FP32, 128, 4, 8),   // T = 512
+    KDE_CFG(KDE_FP32, 64, 8, 8),    // T = 512
+    KDE_CFG(KDE_FP32, 256, 4, 8),   // T = 1024
+    KDE_CFG(KDE_FP32, 64, 4, 8),    // T = 256
+    KDE_CFG(KDE_FP32, 128, 2, 8),   // T = 256
 };
 const ConfigEntry kFp64Configs[] = {
     KDE_CFG(KDE_FP64, 128, 2, 4),   // T = 256
