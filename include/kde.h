@@ -310,7 +310,7 @@ KDE_API kde_status kde_profile_enable(int on);
  * kde_psi.  If cap >= 5, ms[4] is the number of kernel launches of that run
  * (the kernel nodes its CUDA graph replays).  If cap >= 7, ms[5] and ms[6] are
  * the unique pairs the r = 6 and r = 4 pair kernels skipped as far tile pairs
- * (every term below 1e-31 in binary32, exactly 0 in binary64), summed over the
+ * (every term at most |He_r(13.16)| 2^-125 in binary32, exactly 0 in binary64), summed over the
  * run's samples; this waits for the run.  cap >= 4.  KDE_ERR_INVALID if no
  * profiled run happened there. */
 KDE_API kde_status kde_profile_last(void* stream, double* ms, int cap);

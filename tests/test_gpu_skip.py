@@ -1,5 +1,5 @@
 """Far tile pairs: skipped by the pair kernels, counted, and the results still match
-the oracle (binary64 terms there are exactly 0; binary32 ones are below 1e-31)."""
+the oracle (binary64 terms there are exactly 0; binary32 ones are at most |He_r(13.16)| 2^-125)."""
 import numpy as np
 import pytest
 
