@@ -547,6 +547,14 @@ def run_ours(args, ws, rank, local):
                                 "kind": "oracle",
                                 "sample": f"one full PLUGIN run on the same n={n} sample "
                                           f"({pairs_per_step(n)} pair-evals, {dt:.2f} s)"}
+        # the same oracle on one core, on the sample's first 16384 values
+        n1 = min(n, 16384)
+        t0 = time.perf_counter()
+        oracle.plugin(x[:n1], threads=1)
+        dt1 = time.perf_counter() - t0
+        line["cpu_baseline"]["value_1_core"] = pairs_per_step(n1) / dt1
+        line["cpu_baseline"]["sample_1_core"] = (f"one PLUGIN run on the first {n1} values, one thread "
+                                                 f"({pairs_per_step(n1)} pair-evals, {dt1:.2f} s)")
         line["accuracy"]["rel_err_fp32_vs_oracle"] = rel_errors(res32, ref)
         if evl:
             import numpy as np
