@@ -245,8 +245,8 @@ KDE_API kde_status kde_tile_config(kde_precision prec, int64_t n, int32_t* info)
 #define KDE_STATIC_MAX_N 65536
 
 /*
- * kde_psi_static -- psi_r(g) exactly as kde_psi computes it (Steps IV / VI,
- * Eqs. 6-7), for n <= KDE_STATIC_MAX_N, using only a fixed scratch area of
+ * kde_psi_static -- psi_r(g) as kde_psi computes it, for n <= KDE_STATIC_MAX_N,
+ * using only a fixed scratch area of
  * about 1.6 MB compiled into the library as a device variable.  The paper has
  * no counterpart: this exists for callers that must not allocate device memory
  * on the call path, e.g. a process whose framework allocator already holds
@@ -258,8 +258,12 @@ KDE_API kde_status kde_tile_config(kde_precision prec, int64_t n, int32_t* info)
  * Set-up: the first call on a device, with that device current, looks up the
  * scratch area's address once (cudaGetSymbolAddress) and caches it; make that
  * first call before any stream capture meant to contain later calls.
- * Concurrency: one scratch area per device; calls that overlap on the device
- * (other streams or host threads) race on it -- order them on one stream.
+ * Concurrency: one scratch area per device.  Calls from several host threads on
+ * the same stream are serialised by a lock held while the call enqueues its
+ * work; calls that overlap on the device (different streams) race on the area
+ * -- order them on one stream.
+ * Device reset: call kde_shutdown before cudaDeviceReset; the next call then
+ * looks the scratch address up again (and is again a set-up call).
  * Errors: KDE_ERR_INVALID for n > KDE_STATIC_MAX_N (message says so), n < 2,
  * r not in {4, 6, 8, 10}, g <= 0 or not finite, null pointers, a bad precision.
  */
@@ -277,12 +281,16 @@ typedef struct {
     double tick_target_ms;     /* device time per scheduling tick (<= 0: default) */
 } kde_server_config;
 
-/* Per-request timing, host clock, nanoseconds since server creation. */
+/* Per-request timing, host clock, nanoseconds since server creation, and the
+ * unique pairs the r = 6 and r = 4 pair kernels skipped as far tile pairs
+ * (every term below 1e-31 of the diagonal in binary32, exactly 0 in binary64):
+ * the request evaluated n(n-1) - skipped6 - skipped4 pair terms. */
 typedef struct {
     int64_t n;
     int32_t precision;
     int32_t status;
     int64_t t_submit_ns, t_admit_ns, t_done_ns;
+    uint64_t skipped6, skipped4;
 } kde_request_times;
 
 /* Create a server; it reserves its device arena and starts its host thread. */

@@ -58,7 +58,8 @@ class KdeServerConfig(ctypes.Structure):
 class KdeRequestTimes(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int64), ("precision", ctypes.c_int32), ("status", ctypes.c_int32),
                 ("t_submit_ns", ctypes.c_int64), ("t_admit_ns", ctypes.c_int64),
-                ("t_done_ns", ctypes.c_int64)]
+                ("t_done_ns", ctypes.c_int64), ("skipped6", ctypes.c_uint64),
+                ("skipped4", ctypes.c_uint64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

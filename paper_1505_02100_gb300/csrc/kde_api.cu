@@ -709,6 +709,7 @@ void kde_shutdown(void) {
   }
   R.ws.clear();
   eval_release_all();
+  static_scratch_forget();
 }
 
 }  // extern "C"

@@ -160,6 +160,8 @@ int pair_blocks_per_sm(int prec, int cfg);
 kde_status set_err(kde_status s, const std::string& m);
 bool is_device_ptr(const void* p);
 int num_sms();
+// kde_psi_static: forget the cached per-device scratch addresses (kde_shutdown).
+void static_scratch_forget();
 int choose_config(int prec, int64_t n);    // tuner's force, environment, tuned table, built-in rule
 int default_config(int prec, int64_t n);   // the built-in rule
 SampleDesc make_desc(int prec, int cfg, int64_t n, double g_fixed);

@@ -23,6 +23,9 @@
 
 #include <cfloat>
 #include <cmath>
+#include <map>
+#include <mutex>
+#include <tuple>
 
 namespace kde {
 namespace {
@@ -550,6 +553,128 @@ struct Kahan32 {
   }
 };
 
+// ---------------------------------------------------------------------------
+// Binary32 pair terms with the Gaussian factorised over a tile pair
+// ---------------------------------------------------------------------------
+// The sample is sorted, so a row tile and a column sub-tile each hold a narrow
+// range of values.  With row values a_i = a0 + alpha_i, column values
+// b_j = b0 + beta_j and Delta = a0 - b0 (u-units), u = a_i - b_j satisfies
+//   -u^2/2 = -alpha_i (Delta + alpha_i/2) + [beta_j (Delta - beta_j/2) - Delta^2/2]
+//            + alpha_i beta_j,
+// so exp(-u^2/2) = R_i C_j exp(alpha_i beta_j) exactly.  R_i (per row) and C_j
+// (per column, with exp(-Delta^2/2) folded in) are evaluated once per row and
+// column of a sub-tile by an accurate exponential; the coupling factor is
+// 1 + p + p^2/2 with p = alpha_i beta_j, whose truncation error p^3/6 is below
+// 1.7e-10 while |alpha| |beta| <= A B <= kFacPMax (A, B: half-widths of the
+// row tile and the sub-tile).  Every pair term He_r(u^2) exp(-u^2/2) is still
+// evaluated on its own:
+//   u = (a_i - b0) - beta_j,  w = u^2,  He_r(w) by Horner,
+//   e = C_j + alpha_i (C_j beta_j) + (alpha_i^2/2) (C_j beta_j^2),
+//   row sum += He_r(w) e,
+// and R_i multiplies the row's sum once per sub-tile.  The factors carry only
+// rounding errors (no smooth bias), and no term depends on a rounded constant,
+// so the c_lo correction of the polynomial path is not needed here.
+constexpr int kSub = 128;                        // columns per sub-tile (one set of C_j)
+constexpr float kFacPMax = 1.0e-3f;              // A B bound for the 3-term coupling
+constexpr float kFacXMax = 2.0f;                 // |exponent| bound of R_i and of C_j / exp(-Delta^2/2)
+constexpr double kLog2e = 1.4426950408889634074;
+constexpr float kLog2eHi = static_cast<float>(kLog2e);
+constexpr float kLog2eLo = static_cast<float>(kLog2e - static_cast<double>(kLog2eHi));
+
+// e^(xh + xl) in binary32 for a double-float exponent xh + xl <= 3 (|xl| <= 3, xl
+// carrying what xh cannot), 0 below -86 (such factors only reach terms under e^-86
+// of the diagonal).  k = round((xh + xl) log2 e).  xh (log2 e)_hi = ph + pl exactly
+// (product and its FMA residual); ph - k is exact (an integer taken from a nearby
+// binary32), so f = (ph - k) + xl (log2 e)_hi rounds once at |f| <= 1/2, and the
+// small parts pl + xh (log2 e)_lo follow.  2^f by the degree-8 polynomial above,
+// k into the exponent field (a normal result: -125 <= k <= 5).
+__device__ __forceinline__ float exp_factor(float xh, float xl) {
+  const float s = __fadd_rn(xh, xl);
+  if (s < -86.0f) return 0.0f;
+  const float kb = __fmaf_rn(s, kLog2eHi, kRoundMagic);
+  const float kf = __fsub_rn(kb, kRoundMagic);
+  const float ph = __fmul_rn(xh, kLog2eHi);
+  const float pl = __fmaf_rn(xh, kLog2eHi, -ph);
+  float f = __fmaf_rn(xl, kLog2eHi, __fsub_rn(ph, kf));
+  f = __fadd_rn(f, __fmaf_rn(xh, kLog2eLo, pl));
+  return __int_as_float(__float_as_int(exp2_reduced(f)) + (__float_as_int(kb) << 23));
+}
+
+// He_r on w = u^2 with the integer coefficients of Steps IV / VI (and their
+// continuation for r = 8, 10), exact in binary32.
+template <int RORD>
+__device__ __forceinline__ float hermite_w(float w) {
+  if (RORD == 4) return __fmaf_rn(__fadd_rn(w, -6.0f), w, 3.0f);
+  if (RORD == 6) return __fmaf_rn(__fmaf_rn(__fadd_rn(w, -15.0f), w, 45.0f), w, -15.0f);
+  if (RORD == 8)
+    return __fmaf_rn(__fmaf_rn(__fmaf_rn(__fadd_rn(w, -28.0f), w, 210.0f), w, -420.0f), w, 105.0f);
+  return __fmaf_rn(__fmaf_rn(__fmaf_rn(__fmaf_rn(__fadd_rn(w, -45.0f), w, 630.0f), w, -3150.0f), w, 4725.0f),
+                   w, -945.0f);
+}
+
+// The column factors of one sub-tile: fac[j] = (beta_j, C_j, C_j beta_j, C_j beta_j^2)
+// with C_j = exp(beta_j (Delta - beta_j/2) - Delta^2/2); the exponent is formed as
+// a double-float (Delta^2 split exactly by an FMA).  Columns past the sample get
+// zero factors, so their terms vanish.
+template <int THREADS>
+__device__ __forceinline__ void column_factors(const float* __restrict__ tile, const float* __restrict__ tile_lo,
+                                               int vc, float b0, float delta, float4* __restrict__ fac) {
+  const float dh = __fmul_rn(delta, delta);
+  const float dl = __fmaf_rn(delta, delta, -dh);
+#pragma unroll
+  for (int j = threadIdx.x; j < kSub; j += THREADS) {
+    float4 v = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    if (j < vc) {
+      const float beta = __fadd_rn(__fsub_rn(tile[j], b0), tile_lo[j]);
+      const float q = __fmaf_rn(beta, -0.5f, delta);
+      const float xl = __fmaf_rn(beta, q, -0.5f * dl);
+      const float c = exp_factor(-0.5f * dh, xl);
+      const float cb = __fmul_rn(c, beta);
+      v = make_float4(beta, c, cb, __fmul_rn(cb, beta));
+    }
+    fac[j] = v;
+  }
+}
+
+// One sub-tile, factorised: this thread's ROWS rows against kSub columns.
+// ap = a_i - b0, al = alpha_i, ah = alpha_i^2 / 2.  Per row, groups of 8 terms
+// are accumulated by FMA and each group goes into the row's Kahan sum; rs gets
+// the compensated row sums (before R_i).
+template <int RORD, int ROWS>
+__device__ __forceinline__ void tile_pass_fac(const float4* __restrict__ fac, const float (&ap)[ROWS],
+                                              const float (&al)[ROWS], const float (&ah)[ROWS],
+                                              float (&rs)[ROWS]) {
+  float sum[ROWS], comp[ROWS];
+#pragma unroll
+  for (int r = 0; r < ROWS; ++r) sum[r] = comp[r] = 0.0f;
+#pragma unroll 1
+  for (int jj = 0; jj < kSub; jj += 8) {
+    float grp[ROWS];
+#pragma unroll
+    for (int r = 0; r < ROWS; ++r) grp[r] = 0.0f;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const float4 f = fac[jj + q];
+#pragma unroll
+      for (int r = 0; r < ROWS; ++r) {
+        const float u = __fsub_rn(ap[r], f.x);
+        const float h = hermite_w<RORD>(__fmul_rn(u, u));
+        const float e = __fmaf_rn(ah[r], f.w, __fmaf_rn(al[r], f.z, f.y));
+        grp[r] = __fmaf_rn(h, e, grp[r]);
+      }
+    }
+#pragma unroll
+    for (int r = 0; r < ROWS; ++r) {
+      const float y = __fsub_rn(grp[r], comp[r]);
+      const float t = __fadd_rn(sum[r], y);
+      comp[r] = __fsub_rn(__fsub_rn(t, sum[r]), y);
+      sum[r] = t;
+    }
+  }
+#pragma unroll
+  for (int r = 0; r < ROWS; ++r) rs[r] = __fsub_rn(sum[r], comp[r]);
+}
+
 // One tile pair, FP32: this thread's ROWS rows against the TILE columns in
 // shared memory.  Per row, each group of CJ terms (CJ / 4 float4s of columns)
 // is summed as a tree and added to the row's Kahan-compensated sum; the row sums
@@ -629,6 +754,66 @@ __device__ __forceinline__ void tile_pass64(const double* __restrict__ tile,
   acc += seg;
 }
 
+// Binary64 pair terms with the Gaussian factorised over a tile pair: the same
+// identity as the binary32 path (exp(-u^2/2) = R_i C_j exp(alpha_i beta_j)), with
+// the coupling factor taken to p^4/24 (truncation p^5/120 < 3e-19 for
+// |alpha| |beta| <= kFac64PMax) and every factor from the binary64 exp.  Per pair:
+//   u = (a_i - b0) - beta_j,  w = u^2,  He_r(w) by Horner,
+//   e = c0 + alpha (c1 + alpha (c2 + alpha (c3 + alpha c4))),  c_k = C_j beta_j^k / k!,
+//   row sum += He_r(w) e,
+// ten binary64 operations for r = 6 instead of the ~25 of a term with its own exp.
+constexpr double kFac64PMax = 5.0e-4;
+constexpr double kFac64XMax = 8.0;
+
+// Column factors of one sub-tile, three double2 per column:
+// (beta, c0), (c1, c2), (c3, c4); zero past the sample.
+template <int THREADS>
+__device__ __forceinline__ void column_factors64(const double* __restrict__ tile, int vc, double b0,
+                                                 double delta, double2* __restrict__ fac) {
+  const double dh = delta * delta;
+  const double dl = fma(delta, delta, -dh);
+#pragma unroll
+  for (int j = threadIdx.x; j < kSub; j += THREADS) {
+    double2 f0 = make_double2(0.0, 0.0), f1 = f0, f2 = f0;
+    if (j < vc) {
+      const double beta = tile[j] - b0;
+      // beta (delta - beta/2) - delta^2/2, with delta^2 split exactly
+      const double x = fma(beta, fma(beta, -0.5, delta), -0.5 * dh) - 0.5 * dl;
+      const double c0 = exp(x);
+      const double c1 = c0 * beta;
+      const double c2 = c1 * beta * 0.5;
+      const double c3 = c2 * beta * (1.0 / 3.0);
+      const double c4 = c3 * beta * 0.25;
+      f0 = make_double2(beta, c0);
+      f1 = make_double2(c1, c2);
+      f2 = make_double2(c3, c4);
+    }
+    fac[3 * j] = f0;
+    fac[3 * j + 1] = f1;
+    fac[3 * j + 2] = f2;
+  }
+}
+
+// One sub-tile, binary64 factorised: rs gets the row sums (before R_i).
+template <int RORD, int ROWS>
+__device__ __forceinline__ void tile_pass_fac64(const double2* __restrict__ fac, const double (&ap)[ROWS],
+                                                const double (&al)[ROWS], const Coef<double, RORD>& cf,
+                                                double (&rs)[ROWS]) {
+#pragma unroll
+  for (int r = 0; r < ROWS; ++r) rs[r] = 0.0;
+#pragma unroll 2
+  for (int j = 0; j < kSub; ++j) {
+    const double2 f0 = fac[3 * j], f1 = fac[3 * j + 1], f2 = fac[3 * j + 2];
+#pragma unroll
+    for (int r = 0; r < ROWS; ++r) {
+      const double u = __dsub_rn(ap[r], f0.x);
+      const double h = cf.horner(__dmul_rn(u, u));
+      const double e = fma(al[r], fma(al[r], fma(al[r], fma(al[r], f2.y, f2.x), f1.y), f1.x), f0.y);
+      rs[r] = fma(h, e, rs[r]);
+    }
+  }
+}
+
 // Tile pair number p of the upper triangle (I <= J, row by row) -> (I, J).
 // Row I starts at S(I) = I nt - I (I - 1) / 2.
 __device__ __forceinline__ void tri_index(int64_t p, int64_t nt, int64_t& I, int64_t& J) {
@@ -705,8 +890,11 @@ __global__ void __launch_bounds__(THREADS, (pair_min_blocks<PREC, THREADS, ROWS,
   using T = typename Arith<PREC>::T;
   constexpr int TILE = THREADS * ROWS;
   static_assert(TILE % 8 == 0, "tile");
+  static_assert(TILE % kSub == 0, "whole sub-tiles");
   __shared__ __align__(16) T tile[TILE];
   __shared__ __align__(16) float tile_lo[PREC == KDE_FP32 ? TILE : 4];
+  __shared__ __align__(16) float4 fac[PREC == KDE_FP32 ? kSub : 1];
+  __shared__ __align__(16) double2 fac64[PREC == KDE_FP64 ? 3 * kSub : 1];
   __shared__ double red[THREADS / 32 + 1];
   __shared__ long long s_item;
   __shared__ int s_last;
@@ -740,8 +928,18 @@ __global__ void __launch_bounds__(THREADS, (pair_min_blocks<PREC, THREADS, ROWS,
       tri_index(p, d.nt, I, J);
       T w[ROWS];
       float wl[ROWS];
+      // binary32 factorised path: row-tile centre a0 (a grid value), half-width A,
+      // alpha_i = a_i - a0 and alpha_i^2 / 2 per row; first and last valid rows
+      float a0 = 0.0f, halfA = 0.0f, row_first = 0.0f, row_last = 0.0f;
+      float al[ROWS], ah[ROWS];
+      // binary64 factorised path: the same geometry in u-units
+      double a064 = 0.0, halfA64 = 0.0, row_first64 = 0.0, row_last64 = 0.0;
+      double al64[ROWS];
+      unsigned row_ok = 0u;
+      const float unit_f = static_cast<float>(unit);
       // row slot r of this thread holds sample I*TILE + tid*ROWS + r
       auto load_rows = [&](int64_t I_) {
+        row_ok = 0u;
 #pragma unroll
         for (int r = 0; r < ROWS; ++r) {
           const int64_t i = I_ * TILE + static_cast<int64_t>(tid) * ROWS + r;
@@ -749,9 +947,34 @@ __global__ void __launch_bounds__(THREADS, (pair_min_blocks<PREC, THREADS, ROWS,
             const Y v = y[i];
             w[r] = hi_of(v);
             wl[r] = lo_of(v);
+            row_ok |= 1u << r;
           } else {
             w[r] = pad_lo;
             wl[r] = 0.0f;
+          }
+        }
+        if constexpr (PREC == KDE_FP64) {
+          const int64_t vr64 = d.n - I_ * TILE;
+          const int vr = vr64 < TILE ? static_cast<int>(vr64) : TILE;
+          row_first64 = hi_of(y[I_ * TILE]);
+          row_last64 = hi_of(y[I_ * TILE + vr - 1]);
+          a064 = hi_of(y[I_ * TILE + (vr - 1) / 2]);
+          halfA64 = fmax(a064 - row_first64, row_last64 - a064);
+#pragma unroll
+          for (int r = 0; r < ROWS; ++r) al64[r] = ((row_ok >> r) & 1u) ? static_cast<double>(w[r]) - a064 : 0.0;
+        }
+        if constexpr (PREC == KDE_FP32) {
+          const int64_t vr64 = d.n - I_ * TILE;
+          const int vr = vr64 < TILE ? static_cast<int>(vr64) : TILE;
+          row_first = static_cast<float>(hi_of(y[I_ * TILE]));
+          row_last = static_cast<float>(hi_of(y[I_ * TILE + vr - 1]));
+          a0 = static_cast<float>(hi_of(y[I_ * TILE + (vr - 1) / 2]));
+          halfA = __fadd_rn(fmaxf(__fsub_rn(a0, row_first), __fsub_rn(row_last, a0)), unit_f);
+#pragma unroll
+          for (int r = 0; r < ROWS; ++r) {
+            const bool ok = (row_ok >> r) & 1u;
+            al[r] = ok ? __fadd_rn(__fsub_rn(static_cast<float>(w[r]), a0), wl[r]) : 0.0f;
+            ah[r] = __fmul_rn(0.5f, __fmul_rn(al[r], al[r]));
           }
         }
       };
@@ -794,24 +1017,105 @@ __global__ void __launch_bounds__(THREADS, (pair_min_blocks<PREC, THREADS, ROWS,
         __syncthreads();
         // A diagonal tile pair (I == J) is evaluated in full with halved
         // coefficients: the i < j and j < i terms are bitwise equal, and the
-        // i == j terms are He_r(0) / 2 (to the ex2 rounding), removed below.
+        // i == j terms are He_r(0) / 2 (to rounding), removed below.
         const bool diag = (I == J);
         const Coef<T, RORD>& cf = diag ? half : full;
         if constexpr (PREC == KDE_FP32) {
-          // The sample is sorted, so the largest |y_i - y_j| of the tile pair is
-          // its last column minus its first row; tiles with padding always clamp.
-          const double span = static_cast<double>(tile[TILE - 1]) - static_cast<double>(hi_of(y[I * TILE])) + margin;
-          const bool near = (J + 1) * TILE <= d.n && span * span <= static_cast<double>(kWMax);
           const float hf = diag ? 0.5f : 1.0f;
-          if (lo_path) {
-            if (near) tile_pass<RORD, ROWS, CJ, TILE, false, true>(tile, tile_lo, w, wl, hf, acc32, cacc);
-            else tile_pass<RORD, ROWS, CJ, TILE, true, true>(tile, tile_lo, w, wl, hf, acc32, cacc);
-          } else {
-            if (near) tile_pass<RORD, ROWS, CJ, TILE, false, false>(tile, tile_lo, w, wl, hf, acc32, cacc);
-            else tile_pass<RORD, ROWS, CJ, TILE, true, false>(tile, tile_lo, w, wl, hf, acc32, cacc);
+          // the polynomial path clamps on tiles with padding (rows or columns)
+          const bool full_tiles = (J + 1) * TILE <= d.n;
+#pragma unroll 1
+          for (int c0i = 0; c0i < TILE; c0i += kSub) {
+            const int64_t vc64 = d.n - (J * TILE + c0i);
+            if (vc64 <= 0) break;   // the rest of the tile is padding
+            const int vc = vc64 < kSub ? static_cast<int>(vc64) : kSub;
+            const float* __restrict__ sub = tile + c0i;
+            const float* __restrict__ sub_lo = tile_lo + c0i;
+            if (J > I) {   // a far sub-tile: its first column is beyond the clamp from the last row
+              const double gap = static_cast<double>(sub[0]) - static_cast<double>(row_last) - margin;
+              if (gap > 0.0 && gap * gap > far2) {
+                skipped_pairs += static_cast<int64_t>(TILE) * vc;
+                continue;
+              }
+            }
+            const float b0 = sub[(vc - 1) / 2];
+            const float halfB = __fadd_rn(fmaxf(__fsub_rn(b0, sub[0]), __fsub_rn(sub[vc - 1], b0)), unit_f);
+            const float delta = __fsub_rn(a0, b0);
+            const float ad = fabsf(delta);
+            const bool fac_ok = __fmul_rn(halfA, halfB) <= kFacPMax &&
+                                __fmul_rn(halfA, __fadd_rn(ad, halfA)) <= kFacXMax &&
+                                __fmul_rn(halfB, __fadd_rn(ad, halfB)) <= kFacXMax;
+            if (fac_ok) {
+              __syncthreads();   // the previous sub-tile's factors are no longer read
+              column_factors<THREADS>(sub, sub_lo, vc, b0, delta, fac);
+              __syncthreads();
+              float ap[ROWS], rsum[ROWS];
+#pragma unroll
+              for (int r = 0; r < ROWS; ++r)   // rows past the sample: u = -beta_j stays small, R_i = 0
+                ap[r] = ((row_ok >> r) & 1u) ? __fadd_rn(__fsub_rn(static_cast<float>(w[r]), b0), wl[r]) : 0.0f;
+              tile_pass_fac<RORD, ROWS>(fac, ap, al, ah, rsum);
+#pragma unroll
+              for (int r = 0; r < ROWS; ++r) {
+                const float x = -__fmul_rn(al[r], __fmaf_rn(al[r], 0.5f, delta));
+                const float R = ((row_ok >> r) & 1u) ? exp_factor(x, 0.0f) : 0.0f;
+                acc32.add(__fmul_rn(hf, __fmul_rn(rsum[r], R)));
+              }
+            } else {
+              // The largest |y_i - y_j| of the sub-tile against the row tile: its last column
+              // minus the first row, or (on a diagonal tile pair, where rows lie above the
+              // sub-tile too) the last row minus its first column.
+              const double span = fmax(static_cast<double>(sub[kSub - 1]) - static_cast<double>(row_first),
+                                       static_cast<double>(row_last) - static_cast<double>(sub[0])) + margin;
+              const bool near = full_tiles && span * span <= static_cast<double>(kWMax);
+              if (lo_path) {
+                if (near) tile_pass<RORD, ROWS, CJ, kSub, false, true>(sub, sub_lo, w, wl, hf, acc32, cacc);
+                else tile_pass<RORD, ROWS, CJ, kSub, true, true>(sub, sub_lo, w, wl, hf, acc32, cacc);
+              } else {
+                if (near) tile_pass<RORD, ROWS, CJ, kSub, false, false>(sub, sub_lo, w, wl, hf, acc32, cacc);
+                else tile_pass<RORD, ROWS, CJ, kSub, true, false>(sub, sub_lo, w, wl, hf, acc32, cacc);
+              }
+            }
           }
         } else {
-          tile_pass64<RORD, ROWS, TILE>(tile, w, cf, acc64);
+          const double hd = diag ? 0.5 : 1.0;
+#pragma unroll 1
+          for (int c0i = 0; c0i < TILE; c0i += kSub) {
+            const int64_t vc64 = d.n - (J * TILE + c0i);
+            if (vc64 <= 0) break;   // the rest of the tile is padding
+            const int vc = vc64 < kSub ? static_cast<int>(vc64) : kSub;
+            const T* __restrict__ sub = tile + c0i;
+            if (J > I) {   // far sub-tile: every term underflows to exactly 0
+              const double gap = static_cast<double>(sub[0]) - row_last64;
+              if (gap > 0.0 && gap * gap > far2) {
+                skipped_pairs += static_cast<int64_t>(TILE) * vc;
+                continue;
+              }
+            }
+            const double b0 = sub[(vc - 1) / 2];
+            const double halfB = fmax(b0 - sub[0], sub[vc - 1] - b0);
+            const double delta = a064 - b0;
+            const double ad = fabs(delta);
+            const bool fac_ok = halfA64 * halfB <= kFac64PMax && halfA64 * (ad + halfA64) <= kFac64XMax &&
+                                halfB * (ad + halfB) <= kFac64XMax;
+            if (fac_ok) {
+              __syncthreads();   // the previous sub-tile's factors are no longer read
+              column_factors64<THREADS>(sub, vc, b0, delta, fac64);
+              __syncthreads();
+              double ap[ROWS], rsum[ROWS];
+#pragma unroll
+              for (int r = 0; r < ROWS; ++r) ap[r] = ((row_ok >> r) & 1u) ? static_cast<double>(w[r]) - b0 : 0.0;
+              tile_pass_fac64<RORD, ROWS>(fac64, ap, al64, full, rsum);
+              double seg = 0.0;
+#pragma unroll
+              for (int r = 0; r < ROWS; ++r) {
+                const double R = ((row_ok >> r) & 1u) ? exp(-al64[r] * fma(al64[r], 0.5, delta)) : 0.0;
+                seg = fma(rsum[r], R, seg);
+              }
+              acc64 += hd * seg;
+            } else {
+              tile_pass64<RORD, ROWS, kSub>(sub, w, cf, acc64);
+            }
+          }
         }
         if (diag) {
           const int64_t valid = d.n - I * TILE;
@@ -1100,18 +1404,36 @@ int pair_config_count(int prec) {
 
 PairConfig pair_config(int prec, int cfg) { return entry(prec, cfg).cfg; }
 
-int pair_blocks_per_sm(int prec, int cfg) {
-  static int cache[3][8] = {};
-  int& v = cache[prec][cfg];
-  if (v == 0) {
-    const ConfigEntry& e = entry(prec, cfg);
-    int b4 = 0, b6 = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b4, e.k4, e.cfg.threads, 0);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b6, e.k6, e.cfg.threads, 0);
-    v = b4 < b6 ? b4 : b6;
-    if (v < 1) v = 1;
+// Resident blocks per SM of a pair kernel, cached per (device, precision,
+// configuration, order).  Devices of one process may differ, so the current
+// device is part of the key; the cache is shared by every host thread.
+namespace {
+std::mutex g_occ_mu;
+std::map<std::tuple<int, int, int, int>, int> g_occ;
+
+int occupancy_cached(int prec, int cfg, int r, PairKernel k, int threads) {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  const auto key = std::make_tuple(dev, prec, cfg, r);
+  {
+    std::lock_guard<std::mutex> lk(g_occ_mu);
+    const auto it = g_occ.find(key);
+    if (it != g_occ.end()) return it->second;
   }
+  int v = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, k, threads, 0);
+  if (v < 1) v = 1;
+  std::lock_guard<std::mutex> lk(g_occ_mu);
+  g_occ[key] = v;
   return v;
+}
+}  // namespace
+
+int pair_blocks_per_sm(int prec, int cfg) {
+  const ConfigEntry& e = entry(prec, cfg);
+  const int b4 = occupancy_cached(prec, cfg, 4, e.k4, e.cfg.threads);
+  const int b6 = occupancy_cached(prec, cfg, 6, e.k6, e.cfg.threads);
+  return b4 < b6 ? b4 : b6;
 }
 
 cudaError_t launch_stage_results(SampleState* state, int64_t m, cudaStream_t s) {
@@ -1145,13 +1467,7 @@ cudaError_t launch_pairs(int prec, int cfg, const PairArgs& a, int grid, cudaStr
   const ConfigEntry& e = entry(prec, cfg);
   PairKernel k = a.r == 6 ? e.k6 : a.r == 8 ? e.k8 : a.r == 10 ? e.k10 : e.k4;
   if (a.r >= 8) {   // the higher orders may hold more registers: at most their resident count
-    static int cache[3][8][2] = {};
-    int& v = cache[prec][cfg][a.r == 8 ? 0 : 1];
-    if (v == 0) {
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, k, e.cfg.threads, 0);
-      if (v < 1) v = 1;
-    }
-    const int cap = v * num_sms();
+    const int cap = occupancy_cached(prec, cfg, a.r, k, e.cfg.threads) * num_sms();
     if (grid > cap) grid = cap;
   }
   k<<<grid, e.cfg.threads, 0, s>>>(a);

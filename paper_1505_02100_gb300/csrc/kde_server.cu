@@ -469,6 +469,8 @@ struct ServerImpl {
       r->res = s.res;
       r->times.status = s.res.status;
       r->times.t_done_ns = t;
+      r->times.skipped6 = s.skipped[0];
+      r->times.skipped4 = s.skipped[1];
       r->finished = true;
       arena->release(r->off_x, r->b_x);
       arena->release(r->off_y, r->b_y);

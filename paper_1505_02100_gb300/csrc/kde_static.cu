@@ -22,11 +22,16 @@
 // pair block resets the counters again. Nothing else in the scratch area is
 // read before it is written within the same call.
 //
-// Concurrency: there is ONE scratch area per device. Two calls that overlap on
-// the device (different streams, or different host threads) race on it and
-// corrupt each other's results. The host-side lock below guards only the
-// one-time address lookup, so callers must order their calls on the device
-// (for example, issue them all on one stream).
+// Concurrency: there is ONE scratch area per device. A host-side lock is held
+// from the address lookup to the last enqueued operation, so calls from
+// different host threads on the same stream run one after the other on the
+// device. Calls on different streams still overlap on the device and race on
+// the scratch area: callers must order them (for example, issue them all on
+// one stream).
+//
+// Device reset: kde_shutdown forgets the cached addresses, so the first call
+// after a reset (cudaDeviceReset, which reloads the module) looks the address
+// up again. Call kde_shutdown before resetting the device.
 #include "kde_internal.cuh"
 
 #include <cmath>
@@ -78,12 +83,12 @@ __global__ void static_setup_kernel(SampleDesc d, int64_t mblocks, int64_t pbloc
     items[c] = static_cast<uint64_t>(c);   // sample 0, chunk c
 }
 
+// Caller holds g_static_mu.
 kde_status scratch_for_current_device(unsigned char** out) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return set_err(KDE_ERR_CUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e));
   if (dev < 0 || dev >= kMaxDevices) return set_err(KDE_ERR_INVALID, "device ordinal out of range");
-  std::lock_guard<std::mutex> lk(g_static_mu);
   if (!g_static_ptr[dev]) {
     void* p = nullptr;
     e = cudaGetSymbolAddress(&p, g_static_scratch);
@@ -102,6 +107,14 @@ kde_status scratch_for_current_device(unsigned char** out) {
   } while (0)
 
 }  // namespace
+
+// Forget the cached scratch addresses (kde_shutdown; a device reset may move
+// the module).
+void static_scratch_forget() {
+  std::lock_guard<std::mutex> lk(g_static_mu);
+  for (auto& p : g_static_ptr) p = nullptr;
+}
+
 }  // namespace kde
 
 using namespace kde;
@@ -119,6 +132,9 @@ extern "C" kde_status kde_psi_static(const double* x, int64_t n, int r, double g
   if (prec != KDE_FP32 && prec != KDE_FP64 && prec != KDE_Q32) return set_err(KDE_ERR_INVALID, "bad precision");
   if (prec == KDE_Q32 && r > 6) return set_err(KDE_ERR_INVALID, "KDE_Q32 evaluates psi_4 and psi_6 only");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
+  // held until the last operation is enqueued: same-stream calls from several
+  // host threads do not interleave their launches on the one scratch area
+  std::unique_lock<std::mutex> lk(g_static_mu);
   unsigned char* base = nullptr;
   kde_status st = scratch_for_current_device(&base);
   if (st != KDE_OK) return st;
@@ -199,6 +215,7 @@ extern "C" kde_status kde_psi_static(const double* x, int64_t n, int r, double g
   int32_t status = 0;
   KDE_STATIC_CU(cudaMemcpyAsync(&psi, &state->psi_out, sizeof(double), cudaMemcpyDeviceToHost, s));
   KDE_STATIC_CU(cudaMemcpyAsync(&status, &state->res.status, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+  lk.unlock();
   KDE_STATIC_CU(cudaStreamSynchronize(s));
   *out = psi;
   if (status != KDE_OK) return set_err(static_cast<kde_status>(status), "psi failed on device");

@@ -57,6 +57,34 @@ def test_result_struct_layout():
     assert kde.KdeResult.status.offset == 64
 
 
+def test_struct_layouts_match_the_header(tmp_path):
+    """sizeof and every field offset of the public structs, as gcc lays them out
+    from include/kde.h, against the ctypes mirrors of the binding."""
+    import ctypes
+    import subprocess
+
+    import paper_1505_02100_gb300 as kde
+    mirrors = {"kde_result": kde.KdeResult, "kde_stage_result": kde.KdeStageResult,
+               "kde_server_config": kde.KdeServerConfig, "kde_request_times": kde.KdeRequestTimes}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', f'#include "{os.path.join(ROOT, "include", "kde.h")}"',
+             "int main(void) {"]
+    for cname, py in mirrors.items():
+        lines.append(f'  printf("{cname} sizeof %zu\\n", sizeof({cname}));')
+        for fname, _ in py._fields_:
+            lines.append(f'  printf("{cname} {fname} %zu\\n", offsetof({cname}, {fname}));')
+    lines.append("  return 0;\n}")
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-std=c11", "-o", str(exe), str(src)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    got = {(a, b): int(c) for a, b, c in (ln.split() for ln in out if ln.strip())}
+    for cname, py in mirrors.items():
+        assert got[(cname, "sizeof")] == ctypes.sizeof(py), cname
+        for fname, _ in py._fields_:
+            assert got[(cname, fname)] == getattr(py, fname).offset, (cname, fname)
+
+
 def test_errors_without_compute(lib):
     """Argument validation happens before any device work."""
     import ctypes

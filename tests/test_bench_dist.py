@@ -39,7 +39,7 @@ def _rank_main(rank: int, ws: int, port: int, q):
     bench.barrier(w)
     # reference arm: rank 0 prints one JSON line, the others print nothing
     out = io.StringIO()
-    args = argparse.Namespace(gpus=ws, steps=1, warmup=0, n=300)
+    args = argparse.Namespace(gpus=ws, steps=1, warmup=0, ref_n=300)
     with contextlib.redirect_stdout(out):
         bench.run_reference(args, w, r)
     dist.destroy_process_group()

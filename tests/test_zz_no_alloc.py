@@ -1,10 +1,17 @@
-"""kde_psi_static, the allocation-free variant of kde_psi, against kde_psi.
+"""kde_psi_static, the allocation-free variant of kde_psi, against kde_psi and the oracle.
 
-It runs the same kernels on the same plan in a fixed scratch area, so its
-results must agree with kde_psi within the parity tolerances (relative 1e-5
-FP32, 1e-11 FP64); two calls in a row check that no state leaks between calls.
-Collected last so that it also runs after every other GPU test.
+Callers that cannot allocate device memory on their call path use it: a process
+whose framework allocator already holds most of HBM, or a latency-bound loop in
+which cudaMalloc / cudaFree would synchronise the device.  It runs the same
+kernels on the same plan in a fixed scratch area, so its results must agree
+with kde_psi within the parity tolerances (relative 1e-5 FP32, 1e-11 FP64; the
+Q32.32 sums are exact integers, so equal to rounding of the final scaling), and
+with the oracle within the same tolerances.  Two calls in a row check that no
+state leaks from one call to the next.  Collected last so that it also runs
+after every other GPU test.
 """
+import functools
+
 import numpy as np
 import pytest
 
@@ -12,7 +19,7 @@ import synthdata
 
 pytestmark = pytest.mark.gpu
 
-TOL = {0: 1e-5, 1: 1e-11}
+TOL = {0: 1e-5, 1: 1e-11, 2: 1e-12}
 
 
 @pytest.fixture(scope="module")
@@ -30,17 +37,59 @@ def _rel(a, b):
     return abs(a - b) / abs(b)
 
 
+def _sample(n):
+    return synthdata.normal_mixture(900 + n, n, [0.5, 0.5], [-1.0, 1.0], [0.5, 0.5]) + 3.0
+
+
+@functools.lru_cache(maxsize=None)
+def _oracle_psi(n, r, g):
+    import oracle
+    return oracle.psi(_sample(n), r, g)
+
+
+G = {4: 0.2, 6: 0.35, 8: 0.45, 10: 0.55}
+
+
 @pytest.mark.parametrize("prec", [0, 1])
 @pytest.mark.parametrize("r", [4, 6])
 @pytest.mark.parametrize("n", [2, 777, 20000, 65536])
-def test_static_matches_kde_psi_twice(kde, n, r, prec):
-    x = synthdata.normal_mixture(900 + n, n, [0.5, 0.5], [-1.0, 1.0], [0.5, 0.5]) + 3.0
-    g = 0.35 if r == 6 else 0.2
+def test_static_matches_kde_psi_and_oracle_twice(kde, n, r, prec):
+    x = _sample(n)
+    g = G[r]
     ref = kde.kde_psi(x, r, g, prec)
     first = kde.kde_psi_static(x, r, g, prec)
     second = kde.kde_psi_static(x, r, g, prec)
     assert _rel(first, ref) <= TOL[prec], (first, ref)
     assert _rel(second, ref) <= TOL[prec], (second, ref)
+    want = _oracle_psi(n, r, g)
+    assert _rel(first, want) <= TOL[prec], (first, want)
+
+
+@pytest.mark.parametrize("prec,r", [(2, 4), (2, 6), (0, 8), (0, 10), (1, 8), (1, 10)])
+def test_static_other_precisions_and_orders(kde, prec, r):
+    n = 20000
+    x = _sample(n)
+    g = G[r]
+    ref = kde.kde_psi(x, r, g, prec)
+    for _ in range(2):
+        assert _rel(kde.kde_psi_static(x, r, g, prec), ref) <= TOL[prec]
+    if prec != 2:
+        assert _rel(ref, _oracle_psi(n, r, g)) <= TOL[prec]
+
+
+def test_static_call_allocates_no_device_memory(kde):
+    import torch
+    x = torch.tensor(_sample(30000), device="cuda")
+    out = torch.empty(1, dtype=torch.float64, device="cuda")
+    kde.kde_psi_static(x, 6, 0.35, 0, out=out)   # set-up call: address lookup, modules loaded
+    torch.cuda.synchronize()
+    free_before, _ = torch.cuda.mem_get_info()
+    for r in (6, 4, 6):
+        kde.kde_psi_static(x, r, G[r], 0, out=out)
+    torch.cuda.synchronize()
+    free_after, _ = torch.cuda.mem_get_info()
+    assert free_after >= free_before, (free_before, free_after)
+    assert _rel(out.item(), kde.kde_psi(x, 6, 0.35, 0)) <= TOL[0]
 
 
 def test_static_device_input_and_output(kde):
