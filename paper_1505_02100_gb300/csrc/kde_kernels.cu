@@ -404,10 +404,14 @@ __device__ __forceinline__ float lo_of(float2 v) { return v.y; }
 __device__ __forceinline__ double hi_of(double v) { return v; }
 __device__ __forceinline__ float lo_of(double) { return 0.0f; }
 
-// Below this grid exponent the binary32 path adds the rounding residuals to
-// each difference (two more FADDs per pair): rounding to a grid of step
-// g 2^-F would otherwise perturb psi_r by up to ~1e-5 (measured at F = 13).
-constexpr int kFLo = 16;
+// The polynomial (non-factorised) binary32 path always adds the rounding
+// residuals to each difference (two more FADDs per pair), so that every pair term
+// sees the exact data.  Grid values alone would perturb each value by up to half
+// a grid step: on a grid of step g 2^-F that moves psi_r by up to ~1e-5 at F = 13,
+// and even on fine grids the per-tile-pair effect (~1e-6 of a tile pair's sum of
+// |terms|) only cancels over the whole triangle when every pair sees the same
+// rounded data -- it does not once the factorised path (which works on the exact
+// values) takes some of the tile pairs.
 
 // Hermite factor of K^(r) on v = u^2, u = (X_i - X_j)/g, with the integer
 // coefficients printed in Steps IV and VI (exact in binary32):
@@ -556,27 +560,39 @@ struct Kahan32 {
 // ---------------------------------------------------------------------------
 // Binary32 pair terms with the Gaussian factorised over a tile pair
 // ---------------------------------------------------------------------------
-// The sample is sorted, so a row tile and a column sub-tile each hold a narrow
-// range of values.  With row values a_i = a0 + alpha_i, column values
+// The sample is sorted, so a row tile and a segment of a column tile each hold a
+// narrow range of values.  With row values a_i = a0 + alpha_i, column values
 // b_j = b0 + beta_j and Delta = a0 - b0 (u-units), u = a_i - b_j satisfies
 //   -u^2/2 = -alpha_i (Delta + alpha_i/2) + [beta_j (Delta - beta_j/2) - Delta^2/2]
 //            + alpha_i beta_j,
 // so exp(-u^2/2) = R_i C_j exp(alpha_i beta_j) exactly.  R_i (per row) and C_j
 // (per column, with exp(-Delta^2/2) folded in) are evaluated once per row and
-// column of a sub-tile by an accurate exponential; the coupling factor is
-// 1 + p + p^2/2 with p = alpha_i beta_j, whose truncation error p^3/6 is below
-// 1.7e-10 while |alpha| |beta| <= A B <= kFacPMax (A, B: half-widths of the
-// row tile and the sub-tile).  Every pair term He_r(u^2) exp(-u^2/2) is still
-// evaluated on its own:
+// column of a segment by an accurate exponential; the coupling factor is the
+// Taylor polynomial of exp(p), p = alpha_i beta_j, to order K:
+//   K = 2: 1 + p + p^2/2, truncation p^3/6 <= 1.7e-10 while A B <= kFacP2,
+//   K = 1: 1 + p,         truncation p^2/2 <= 8e-12   while A B <= kFacP1
+// (A, B: half-widths of the row tile and the segment).  Every pair term
+// He_r(u^2) exp(-u^2/2) is still evaluated on its own:
 //   u = (a_i - b0) - beta_j,  w = u^2,  He_r(w) by Horner,
-//   e = C_j + alpha_i (C_j beta_j) + (alpha_i^2/2) (C_j beta_j^2),
+//   e = C_j + alpha_i (C_j beta_j) [+ (alpha_i^2/2) (C_j beta_j^2)],
 //   row sum += He_r(w) e,
-// and R_i multiplies the row's sum once per sub-tile.  The factors carry only
-// rounding errors (no smooth bias), and no term depends on a rounded constant,
-// so the c_lo correction of the polynomial path is not needed here.
-constexpr int kSub = 128;                        // columns per sub-tile (one set of C_j)
-constexpr float kFacPMax = 1.0e-3f;              // A B bound for the 3-term coupling
+// and R_i multiplies the row's sum once per segment: r/2 + 4 (K = 1) or r/2 + 5
+// (K = 2) FMA-pipe operations per pair.  The factors carry only rounding errors
+// (no smooth bias), and no term depends on a rounded constant, so the c_lo
+// correction of the polynomial path is not needed here.
+//
+// Segments are aligned power-of-two column ranges of 32 ... 512.  A tile pair
+// takes one width and order from the column tile's overall half-width (the
+// cheaper of K = 1 at the widest width it allows and K = 2 at the widest width
+// it allows, each segment costing ~kRowCost operations per row); every segment
+// then checks its own half-width and falls back to K = 2, or to the polynomial
+// path, where needed.
+constexpr int kSub = 128;                        // columns per binary64 sub-tile
+constexpr int kSegMax = 512, kSegMin = 32;       // binary32 segment widths
+constexpr float kFacP1 = 4.0e-6f;                // A B bound for the 2-term coupling
+constexpr float kFacP2 = 1.0e-3f;                // A B bound for the 3-term coupling
 constexpr float kFacXMax = 2.0f;                 // |exponent| bound of R_i and of C_j / exp(-Delta^2/2)
+constexpr float kRowCost = 26.0f;                // operations per row and segment (R_i, the fold)
 constexpr double kLog2e = 1.4426950408889634074;
 constexpr float kLog2eHi = static_cast<float>(kLog2e);
 constexpr float kLog2eLo = static_cast<float>(kLog2e - static_cast<double>(kLog2eHi));
@@ -600,6 +616,17 @@ __device__ __forceinline__ float exp_factor(float xh, float xl) {
   return __int_as_float(__float_as_int(exp2_reduced(f)) + (__float_as_int(kb) << 23));
 }
 
+// e^x for |x| <= 3 (the row factors): k = round(x log2 e), f = x (log2 e)_hi - k
+// from the exact product minus an integer, rounded once (|f| <= 1/2), plus
+// x (log2 e)_lo; 2^f by the degree-8 polynomial, k into the exponent field.
+__device__ __forceinline__ float exp_small(float x) {
+  const float kb = __fmaf_rn(x, kLog2eHi, kRoundMagic);
+  const float kf = __fsub_rn(kb, kRoundMagic);
+  float f = __fmaf_rn(x, kLog2eHi, -kf);
+  f = __fmaf_rn(x, kLog2eLo, f);
+  return __int_as_float(__float_as_int(exp2_reduced(f)) + (__float_as_int(kb) << 23));
+}
+
 // He_r on w = u^2 with the integer coefficients of Steps IV / VI (and their
 // continuation for r = 8, 10), exact in binary32.
 template <int RORD>
@@ -612,17 +639,17 @@ __device__ __forceinline__ float hermite_w(float w) {
                    w, -945.0f);
 }
 
-// The column factors of one sub-tile: fac[j] = (beta_j, C_j, C_j beta_j, C_j beta_j^2)
-// with C_j = exp(beta_j (Delta - beta_j/2) - Delta^2/2); the exponent is formed as
-// a double-float (Delta^2 split exactly by an FMA).  Columns past the sample get
-// zero factors, so their terms vanish.
+// The column factors of one segment of `width` columns: fac[j] = (beta_j, C_j,
+// C_j beta_j, C_j beta_j^2) with C_j = exp(beta_j (Delta - beta_j/2) - Delta^2/2);
+// the exponent is formed as a double-float (Delta^2 split exactly by an FMA).
+// Columns past the sample (j >= vc) get zero factors, so their terms vanish.
 template <int THREADS>
 __device__ __forceinline__ void column_factors(const float* __restrict__ tile, const float* __restrict__ tile_lo,
-                                               int vc, float b0, float delta, float4* __restrict__ fac) {
+                                               int width, int vc, float b0, float delta,
+                                               float4* __restrict__ fac) {
   const float dh = __fmul_rn(delta, delta);
   const float dl = __fmaf_rn(delta, delta, -dh);
-#pragma unroll
-  for (int j = threadIdx.x; j < kSub; j += THREADS) {
+  for (int j = threadIdx.x; j < width; j += THREADS) {
     float4 v = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
     if (j < vc) {
       const float beta = __fadd_rn(__fsub_rn(tile[j], b0), tile_lo[j]);
@@ -636,30 +663,32 @@ __device__ __forceinline__ void column_factors(const float* __restrict__ tile, c
   }
 }
 
-// One sub-tile, factorised: this thread's ROWS rows against kSub columns.
-// ap = a_i - b0, al = alpha_i, ah = alpha_i^2 / 2.  Per row, groups of 8 terms
-// are accumulated by FMA and each group goes into the row's Kahan sum; rs gets
-// the compensated row sums (before R_i).
-template <int RORD, int ROWS>
-__device__ __forceinline__ void tile_pass_fac(const float4* __restrict__ fac, const float (&ap)[ROWS],
+// One segment, factorised: this thread's ROWS rows against `width` columns (a
+// multiple of 16).  ap = a_i - b0, al = alpha_i, ah = alpha_i^2 / 2.  Per row,
+// groups of 16 terms are accumulated by FMA (one rounding per term, the product
+// exact) and each group goes into the row's Kahan sum; rs gets the compensated
+// row sums (before R_i).
+template <int RORD, int ROWS, int K>
+__device__ __forceinline__ void tile_pass_fac(const float4* __restrict__ fac, int width, const float (&ap)[ROWS],
                                               const float (&al)[ROWS], const float (&ah)[ROWS],
                                               float (&rs)[ROWS]) {
   float sum[ROWS], comp[ROWS];
 #pragma unroll
   for (int r = 0; r < ROWS; ++r) sum[r] = comp[r] = 0.0f;
 #pragma unroll 1
-  for (int jj = 0; jj < kSub; jj += 8) {
+  for (int jj = 0; jj < width; jj += 16) {
     float grp[ROWS];
 #pragma unroll
     for (int r = 0; r < ROWS; ++r) grp[r] = 0.0f;
 #pragma unroll
-    for (int q = 0; q < 8; ++q) {
+    for (int q = 0; q < 16; ++q) {
       const float4 f = fac[jj + q];
 #pragma unroll
       for (int r = 0; r < ROWS; ++r) {
         const float u = __fsub_rn(ap[r], f.x);
         const float h = hermite_w<RORD>(__fmul_rn(u, u));
-        const float e = __fmaf_rn(ah[r], f.w, __fmaf_rn(al[r], f.z, f.y));
+        float e = __fmaf_rn(al[r], f.z, f.y);
+        if (K == 2) e = __fmaf_rn(ah[r], f.w, e);
         grp[r] = __fmaf_rn(h, e, grp[r]);
       }
     }
@@ -683,16 +712,16 @@ __device__ __forceinline__ void tile_pass_fac(const float4* __restrict__ fac, co
 // summation of such runs drifts systematically, which the cancellation of the
 // pair sum would amplify.  Per row, sum(term * v) feeds the c_lo correction
 // (see term32), which goes to the thread's binary64 total `cacc`.
-template <int RORD, int ROWS, int CJ, int TILE, bool CLAMP, bool LO>
+template <int RORD, int ROWS, int CJ, bool CLAMP, bool LO>
 __device__ __forceinline__ void tile_pass(const float* __restrict__ tile, const float* __restrict__ tile_lo,
-                                          const float (&w)[ROWS], const float (&wl)[ROWS], float half,
+                                          int ncol, const float (&w)[ROWS], const float (&wl)[ROWS], float half,
                                           Kahan32& acc, double& cacc) {
   static_assert(CJ == 4 || CJ == 8, "one or two float4s of columns per group of terms");
   float sum[ROWS], comp[ROWS], tv[ROWS];
 #pragma unroll
   for (int r = 0; r < ROWS; ++r) sum[r] = comp[r] = tv[r] = 0.0f;
 #pragma unroll 1
-  for (int jj = 0; jj < TILE; jj += CJ) {
+  for (int jj = 0; jj < ncol; jj += CJ) {
     float b[CJ], bl[CJ];
 #pragma unroll
     for (int q4 = 0; q4 < CJ; q4 += 4) {
@@ -893,7 +922,7 @@ __global__ void __launch_bounds__(THREADS, (pair_min_blocks<PREC, THREADS, ROWS,
   static_assert(TILE % kSub == 0, "whole sub-tiles");
   __shared__ __align__(16) T tile[TILE];
   __shared__ __align__(16) float tile_lo[PREC == KDE_FP32 ? TILE : 4];
-  __shared__ __align__(16) float4 fac[PREC == KDE_FP32 ? kSub : 1];
+  __shared__ __align__(16) float4 fac[PREC == KDE_FP32 ? (kSegMax < TILE ? kSegMax : TILE) : 1];
   __shared__ __align__(16) double2 fac64[PREC == KDE_FP64 ? 3 * kSub : 1];
   __shared__ double red[THREADS / 32 + 1];
   __shared__ long long s_item;
@@ -978,7 +1007,6 @@ __global__ void __launch_bounds__(THREADS, (pair_min_blocks<PREC, THREADS, ROWS,
           }
         }
       };
-      const bool lo_path = PREC == KDE_FP32 && st->F < kFLo;
       const double margin = PREC == KDE_FP32 ? unit : 0.0;   // |residual differences| <= 1 grid unit
       load_rows(I);
       Kahan32 acc32;
@@ -1024,14 +1052,35 @@ __global__ void __launch_bounds__(THREADS, (pair_min_blocks<PREC, THREADS, ROWS,
           const float hf = diag ? 0.5f : 1.0f;
           // the polynomial path clamps on tiles with padding (rows or columns)
           const bool full_tiles = (J + 1) * TILE <= d.n;
+          const int64_t vct64 = d.n - J * TILE;
+          const int vct = vct64 < TILE ? static_cast<int>(vct64) : TILE;
+          // width and coupling order of the tile pair's segments, estimated from the
+          // column tile's half-width scaled to each width (each segment checks its own)
+          int kord = 0, segw = kSub;
+          {
+            const float abt = __fmul_rn(halfA, __fadd_rn(__fmul_rn(0.5f, __fsub_rn(tile[vct - 1], tile[0])), unit_f));
+            int w1 = 0, w2 = 0;
+#pragma unroll
+            for (int wd = (kSegMax < TILE ? kSegMax : TILE); wd >= kSegMin; wd >>= 1) {
+              const float est = abt * (static_cast<float>(wd) / static_cast<float>(TILE));
+              if (w2 == 0 && est <= kFacP2) w2 = wd;
+              if (w1 == 0 && est <= kFacP1) w1 = wd;
+            }
+            if (w1 > 0 && kRowCost / static_cast<float>(w1) <=
+                              (w2 > 0 ? 1.0f + kRowCost / static_cast<float>(w2) : 1e30f)) {
+              kord = 1;
+              segw = w1;
+            } else if (w2 > 0) {
+              kord = 2;
+              segw = w2;
+            }
+          }
 #pragma unroll 1
-          for (int c0i = 0; c0i < TILE; c0i += kSub) {
-            const int64_t vc64 = d.n - (J * TILE + c0i);
-            if (vc64 <= 0) break;   // the rest of the tile is padding
-            const int vc = vc64 < kSub ? static_cast<int>(vc64) : kSub;
+          for (int c0i = 0; c0i < vct; c0i += segw) {
+            const int vc = vct - c0i < segw ? vct - c0i : segw;
             const float* __restrict__ sub = tile + c0i;
             const float* __restrict__ sub_lo = tile_lo + c0i;
-            if (J > I) {   // a far sub-tile: its first column is beyond the clamp from the last row
+            if (J > I) {   // a far segment: its first column is beyond the clamp from the last row
               const double gap = static_cast<double>(sub[0]) - static_cast<double>(row_last) - margin;
               if (gap > 0.0 && gap * gap > far2) {
                 skipped_pairs += static_cast<int64_t>(TILE) * vc;
@@ -1042,38 +1091,35 @@ __global__ void __launch_bounds__(THREADS, (pair_min_blocks<PREC, THREADS, ROWS,
             const float halfB = __fadd_rn(fmaxf(__fsub_rn(b0, sub[0]), __fsub_rn(sub[vc - 1], b0)), unit_f);
             const float delta = __fsub_rn(a0, b0);
             const float ad = fabsf(delta);
-            const bool fac_ok = __fmul_rn(halfA, halfB) <= kFacPMax &&
-                                __fmul_rn(halfA, __fadd_rn(ad, halfA)) <= kFacXMax &&
-                                __fmul_rn(halfB, __fadd_rn(ad, halfB)) <= kFacXMax;
-            if (fac_ok) {
-              __syncthreads();   // the previous sub-tile's factors are no longer read
-              column_factors<THREADS>(sub, sub_lo, vc, b0, delta, fac);
+            const float ab = __fmul_rn(halfA, halfB);
+            const bool xok = __fmul_rn(halfA, __fadd_rn(ad, halfA)) <= kFacXMax &&
+                             __fmul_rn(halfB, __fadd_rn(ad, halfB)) <= kFacXMax;
+            const int K = !xok ? 0 : (kord == 1 && ab <= kFacP1) ? 1 : (ab <= kFacP2 ? 2 : 0);
+            if (K > 0) {
+              __syncthreads();   // the previous segment's factors are no longer read
+              column_factors<THREADS>(sub, sub_lo, segw, vc, b0, delta, fac);
               __syncthreads();
               float ap[ROWS], rsum[ROWS];
 #pragma unroll
               for (int r = 0; r < ROWS; ++r)   // rows past the sample: u = -beta_j stays small, R_i = 0
                 ap[r] = ((row_ok >> r) & 1u) ? __fadd_rn(__fsub_rn(static_cast<float>(w[r]), b0), wl[r]) : 0.0f;
-              tile_pass_fac<RORD, ROWS>(fac, ap, al, ah, rsum);
+              if (K == 1) tile_pass_fac<RORD, ROWS, 1>(fac, segw, ap, al, ah, rsum);
+              else tile_pass_fac<RORD, ROWS, 2>(fac, segw, ap, al, ah, rsum);
 #pragma unroll
               for (int r = 0; r < ROWS; ++r) {
                 const float x = -__fmul_rn(al[r], __fmaf_rn(al[r], 0.5f, delta));
-                const float R = ((row_ok >> r) & 1u) ? exp_factor(x, 0.0f) : 0.0f;
+                const float R = ((row_ok >> r) & 1u) ? exp_small(x) : 0.0f;
                 acc32.add(__fmul_rn(hf, __fmul_rn(rsum[r], R)));
               }
             } else {
-              // The largest |y_i - y_j| of the sub-tile against the row tile: its last column
+              // The largest |y_i - y_j| of the segment against the row tile: its last column
               // minus the first row, or (on a diagonal tile pair, where rows lie above the
-              // sub-tile too) the last row minus its first column.
-              const double span = fmax(static_cast<double>(sub[kSub - 1]) - static_cast<double>(row_first),
+              // segment too) the last row minus its first column.
+              const double span = fmax(static_cast<double>(sub[vc - 1]) - static_cast<double>(row_first),
                                        static_cast<double>(row_last) - static_cast<double>(sub[0])) + margin;
               const bool near = full_tiles && span * span <= static_cast<double>(kWMax);
-              if (lo_path) {
-                if (near) tile_pass<RORD, ROWS, CJ, kSub, false, true>(sub, sub_lo, w, wl, hf, acc32, cacc);
-                else tile_pass<RORD, ROWS, CJ, kSub, true, true>(sub, sub_lo, w, wl, hf, acc32, cacc);
-              } else {
-                if (near) tile_pass<RORD, ROWS, CJ, kSub, false, false>(sub, sub_lo, w, wl, hf, acc32, cacc);
-                else tile_pass<RORD, ROWS, CJ, kSub, true, false>(sub, sub_lo, w, wl, hf, acc32, cacc);
-              }
+              if (near) tile_pass<RORD, ROWS, CJ, false, true>(sub, sub_lo, segw, w, wl, hf, acc32, cacc);
+              else tile_pass<RORD, ROWS, CJ, true, true>(sub, sub_lo, segw, w, wl, hf, acc32, cacc);
             }
           }
         } else {

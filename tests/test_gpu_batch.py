@@ -64,18 +64,36 @@ def test_batch_device_resident_and_replay(kde):
         assert first[k]["status"] == 0
 
 
-def test_full_batch_workload_statuses_and_spot_checks(kde):
-    """The 512-sample workload (n log-uniform in [256, 262144]): all succeed; the
-    smallest samples match the oracle and a few match their stand-alone runs."""
+def _golden(kind):
+    import os
+    import sys
+    sys.path.insert(0, os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden"))
+    import make_golden
+    return make_golden.load(kind)
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_full_batch_workload_against_oracle(kde, prec):
+    """The 512-sample workload (n log-uniform in [256, 262144]): all succeed, every
+    sample with a stored oracle value (all n <= 65536, and larger ones where stored)
+    matches it (1e-5 FP32, 1e-11 FP64), and a few match their stand-alone runs."""
     specs = synthdata.batch_specs()
     samples = [synthdata.sample_from_spec(s) for s in specs]
     x, off = _pack(samples)
-    got = kde.kde_plugin_h_batch(x, off, 0)
+    got = kde.kde_plugin_h_batch(x, off, prec)
     assert all(r["status"] == 0 for r in got)
+    gold = _golden("batch")
+    tol = 1e-5 if prec == 0 else 1e-11
+    checked = 0
+    for k, spec in enumerate(specs):
+        ref = gold.get(str(spec.index))
+        if ref is None:
+            continue
+        assert ref["n"] == spec.n
+        for f in ("psi6", "g2", "psi4", "h"):
+            assert abs(got[k][f] - ref[f]) <= tol * abs(ref[f]), (k, spec.n, f, got[k][f], ref[f])
+        checked += 1
+    assert checked >= sum(s.n <= 65536 for s in specs)
     order = np.argsort([s.size for s in samples])
-    for k in order[:6]:
-        ref = oracle.plugin(samples[k])
-        for f in ("psi6", "psi4", "h"):
-            assert abs(got[k][f] - ref[f]) <= 1e-5 * abs(ref[f]), (k, f)
     for k in list(order[-2:]) + [int(order[len(order) // 2])]:
-        assert got[k] == kde.kde_plugin_h(samples[k], 0)
+        assert got[k] == kde.kde_plugin_h(samples[k], prec)

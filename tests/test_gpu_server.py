@@ -1,5 +1,6 @@
 """Continuous-batching server: results are those of the stand-alone call, alone or
-in the mix, and every request carries submit/admit/done times."""
+in the mix, they match the oracle on the served stream, and every request carries
+submit/admit/done times and its skipped-pair counts."""
 import threading
 import time
 
@@ -88,3 +89,43 @@ def test_server_concurrent_clients(kde):
             t.join()
     for k, s in enumerate(samples):
         assert out[k][0] == kde.kde_plugin_h(s, 0)
+
+
+def test_served_stream_against_oracle(kde):
+    """A mix from the served stream (n log-uniform in [1000, 4194304], binary32
+    samples): requests with n <= 65536 whose oracle values are stored, interleaved
+    with larger ones, arriving while others run.  Each stored request matches the
+    oracle (1e-5 FP32; a few served in FP64 at 1e-11), every request equals its
+    stand-alone call bitwise, and n(n-1) minus the skipped pairs is what ran."""
+    import os
+    import sys
+    sys.path.insert(0, os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden"))
+    import make_golden
+    gold = make_golden.load("serve")
+    specs = synthdata.server_specs()[:1000]
+    small = [s for s in specs if str(s.index) in gold][:48]
+    large = [s for s in specs if 65536 < s.n <= 400000][:4]
+    mix = sorted(small + large, key=lambda s: s.index)
+    xs = [synthdata.sample_from_spec(s, np.float32) for s in mix]
+    precs = [1 if (k % 9 == 4 and s.n <= 65536) else 0 for k, s in enumerate(mix)]
+    with kde.Server(hbm_budget_bytes=4 << 30, max_inflight=64, tick_target_ms=2.0) as srv:
+        tickets = []
+        for k, x in enumerate(xs):
+            tickets.append(srv.submit(x, precs[k]))
+            if k % 4 == 0:
+                time.sleep(0.003)
+        results = [srv.poll(t, timeout_ms=300000) for t in tickets]
+    n_fp64 = 0
+    for k, (spec, x) in enumerate(zip(mix, xs)):
+        res, times = results[k]
+        assert res["status"] == 0, k
+        assert res == kde.kde_plugin_h(x, precs[k]), k
+        assert times["skipped6"] + times["skipped4"] < x.size * (x.size - 1)
+        ref = gold.get(str(spec.index))
+        if ref is None:
+            continue
+        tol = 1e-11 if precs[k] else 1e-5
+        n_fp64 += precs[k]
+        for f in ("psi6", "g2", "psi4", "h"):
+            assert abs(res[f] - ref[f]) <= tol * abs(ref[f]), (spec.index, precs[k], f, res[f], ref[f])
+    assert n_fp64 >= 3
