@@ -584,15 +584,18 @@ struct Kahan32 {
 // Segments are aligned power-of-two column ranges of 32 ... 512.  A tile pair
 // takes one width and order from the column tile's overall half-width (the
 // cheaper of K = 1 at the widest width it allows and K = 2 at the widest width
-// it allows, each segment costing ~kRowCost operations per row); every segment
+// it allows); every segment
 // then checks its own half-width and falls back to K = 2, or to the polynomial
-// path, where needed.
+// path, where needed.  A segment of width w costs each thread about
+// (kSegRowOps + kSegFixedOps / ROWS) / w slots per pair on top of the pairs.
 constexpr int kSub = 128;                        // columns per binary64 sub-tile
 constexpr int kSegMax = 512, kSegMin = 32;       // binary32 segment widths
 constexpr float kFacP1 = 4.0e-6f;                // A B bound for the 2-term coupling
 constexpr float kFacP2 = 1.0e-3f;                // A B bound for the 3-term coupling
 constexpr float kFacXMax = 2.0f;                 // |exponent| bound of R_i and of C_j / exp(-Delta^2/2)
-constexpr float kRowCost = 26.0f;                // operations per row and segment (R_i, the fold)
+// Issue slots a segment costs each thread, beyond its pairs: ~24 per row (R_i, the
+// fold into the accumulator) and ~50 shared (column factors, barriers, the checks).
+constexpr float kSegRowOps = 24.0f, kSegFixedOps = 50.0f;
 constexpr double kLog2e = 1.4426950408889634074;
 constexpr float kLog2eHi = static_cast<float>(kLog2e);
 constexpr float kLog2eLo = static_cast<float>(kLog2e - static_cast<double>(kLog2eHi));
@@ -844,11 +847,13 @@ __device__ __forceinline__ void tile_pass_fac64(const double2* __restrict__ fac,
 }
 
 // Tile pair number p of the upper triangle (I <= J, row by row) -> (I, J).
-// Row I starts at S(I) = I nt - I (I - 1) / 2.
+// Row I starts at S(I) = I nt - I (I - 1) / 2.  The root of the quadratic gives a
+// first guess (binary32: a few rows off at most for nt <= 2^16, which the integer
+// steps below correct exactly).
 __device__ __forceinline__ void tri_index(int64_t p, int64_t nt, int64_t& I, int64_t& J) {
-  const double b = 2.0 * static_cast<double>(nt) + 1.0;
-  const double disc = fmax(b * b - 8.0 * static_cast<double>(p), 0.0);
-  int64_t i = static_cast<int64_t>(floor((b - sqrt(disc)) * 0.5));
+  const float b = 2.0f * static_cast<float>(nt) + 1.0f;
+  const float disc = fmaxf(b * b - 8.0f * static_cast<float>(p), 0.0f);
+  int64_t i = static_cast<int64_t>(floorf((b - sqrtf(disc)) * 0.5f));
   if (i > nt - 1) i = nt - 1;
   if (i < 0) i = 0;
   auto S = [nt](int64_t q) { return q * nt - q * (q - 1) / 2; };
@@ -941,7 +946,7 @@ __global__ void __launch_bounds__(THREADS, (pair_min_blocks<PREC, THREADS, ROWS,
     SampleState* st = a.state + k;
 
     double part = 0.0;
-    double diag_units = 0.0;
+    int64_t diag_units = 0;
     if (st->res.status == KDE_OK) {
       using Y = typename Arith<PREC>::Y;
       const Y* __restrict__ y = static_cast<const Y*>(a.y) + d.y_off;
@@ -953,6 +958,7 @@ __global__ void __launch_bounds__(THREADS, (pair_min_blocks<PREC, THREADS, ROWS,
       half.set(0.5, 1.0);
       int64_t p = c * d.chunk;
       const int64_t pend = (p + d.chunk < d.ntp) ? p + d.chunk : d.ntp;
+      // the first tile pair of the chunk
       int64_t I, J;
       tri_index(p, d.nt, I, J);
       T w[ROWS];
@@ -1007,7 +1013,6 @@ __global__ void __launch_bounds__(THREADS, (pair_min_blocks<PREC, THREADS, ROWS,
           }
         }
       };
-      const double margin = PREC == KDE_FP32 ? unit : 0.0;   // |residual differences| <= 1 grid unit
       load_rows(I);
       Kahan32 acc32;
       double cacc = 0.0;
@@ -1021,9 +1026,13 @@ __global__ void __launch_bounds__(THREADS, (pair_min_blocks<PREC, THREADS, ROWS,
       for (; p < pend; ++p) {
         bool far = false;
         if (J > I) {
-          const double gap = static_cast<double>(hi_of(y[J * TILE])) -
-                             static_cast<double>(hi_of(y[I * TILE + TILE - 1])) - margin;
-          far = gap > 0.0 && gap * gap > far2;
+          if constexpr (PREC == KDE_FP32) {   // binary32 on the grid (block-uniform test)
+            const float gap = __fsub_rn(__fsub_rn(hi_of(y[J * TILE]), hi_of(y[I * TILE + TILE - 1])), unit_f);
+            far = gap > 0.0f && __fmul_rn(gap, gap) > kWMax;
+          } else {
+            const double gap = static_cast<double>(hi_of(y[J * TILE])) - static_cast<double>(hi_of(y[I * TILE + TILE - 1]));
+            far = gap > 0.0 && gap * gap > far2;
+          }
         }
         if (far) {
           const int64_t cols = d.n - J * TILE;
@@ -1066,8 +1075,9 @@ __global__ void __launch_bounds__(THREADS, (pair_min_blocks<PREC, THREADS, ROWS,
               if (w2 == 0 && est <= kFacP2) w2 = wd;
               if (w1 == 0 && est <= kFacP1) w1 = wd;
             }
-            if (w1 > 0 && kRowCost / static_cast<float>(w1) <=
-                              (w2 > 0 ? 1.0f + kRowCost / static_cast<float>(w2) : 1e30f)) {
+            constexpr float seg_cost = kSegRowOps + kSegFixedOps / ROWS;
+            if (w1 > 0 && seg_cost / static_cast<float>(w1) <=
+                              (w2 > 0 ? 1.0f + seg_cost / static_cast<float>(w2) : 1e30f)) {
               kord = 1;
               segw = w1;
             } else if (w2 > 0) {
@@ -1081,8 +1091,8 @@ __global__ void __launch_bounds__(THREADS, (pair_min_blocks<PREC, THREADS, ROWS,
             const float* __restrict__ sub = tile + c0i;
             const float* __restrict__ sub_lo = tile_lo + c0i;
             if (J > I) {   // a far segment: its first column is beyond the clamp from the last row
-              const double gap = static_cast<double>(sub[0]) - static_cast<double>(row_last) - margin;
-              if (gap > 0.0 && gap * gap > far2) {
+              const float gap = __fsub_rn(__fsub_rn(sub[0], row_last), unit_f);
+              if (gap > 0.0f && __fmul_rn(gap, gap) > kWMax) {
                 skipped_pairs += static_cast<int64_t>(TILE) * vc;
                 continue;
               }
@@ -1115,9 +1125,9 @@ __global__ void __launch_bounds__(THREADS, (pair_min_blocks<PREC, THREADS, ROWS,
               // The largest |y_i - y_j| of the segment against the row tile: its last column
               // minus the first row, or (on a diagonal tile pair, where rows lie above the
               // segment too) the last row minus its first column.
-              const double span = fmax(static_cast<double>(sub[vc - 1]) - static_cast<double>(row_first),
-                                       static_cast<double>(row_last) - static_cast<double>(sub[0])) + margin;
-              const bool near = full_tiles && span * span <= static_cast<double>(kWMax);
+              const float span = __fadd_rn(fmaxf(__fsub_rn(sub[vc - 1], row_first), __fsub_rn(row_last, sub[0])),
+                                           unit_f);
+              const bool near = full_tiles && __fmul_rn(span, span) <= kWMax;
               if (near) tile_pass<RORD, ROWS, CJ, false, true>(sub, sub_lo, segw, w, wl, hf, acc32, cacc);
               else tile_pass<RORD, ROWS, CJ, true, true>(sub, sub_lo, segw, w, wl, hf, acc32, cacc);
             }
@@ -1165,7 +1175,7 @@ __global__ void __launch_bounds__(THREADS, (pair_min_blocks<PREC, THREADS, ROWS,
         }
         if (diag) {
           const int64_t valid = d.n - I * TILE;
-          diag_units += static_cast<double>(valid < TILE ? valid : TILE);
+          diag_units += valid < TILE ? valid : TILE;
         }
         }
         if (++J == d.nt) {
@@ -1180,7 +1190,7 @@ __global__ void __launch_bounds__(THREADS, (pair_min_blocks<PREC, THREADS, ROWS,
     }
     const double tot = block_sum<THREADS>(part, red);
     if (tid == 0) {
-      a.slots[d.slot_off + c] = tot - 0.5 * he_at_zero<RORD>() * diag_units;
+      a.slots[d.slot_off + c] = tot - 0.5 * he_at_zero<RORD>() * static_cast<double>(diag_units);
       __threadfence();
       const unsigned prev = atomicAdd(&st->done_pairs, 1u);
       s_last = (prev + 1 == static_cast<unsigned>(d.nchunks));
