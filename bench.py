@@ -58,12 +58,12 @@ REF_N = 65536          # reference arm: oracle on the first REF_N values of each
 CPU_N = 98304          # cpu_baseline: oracle on the first CPU_N values of each sample
 RESULT_FIELDS = ("psi6", "psi4", "h")
 
-# Issue slots per pair of the binary32 kernel's factorised sequence (tile pairs
-# whose rows and columns are narrow, >99.8% of the evaluated pairs here):
-# FADD u, FMUL w, Horner He_r (FADD + r/2 - 1 FFMA), 2 FFMA for the coupling
-# factor, FFMA accumulate, 4/8 for one Kahan step per 8 terms, and one LDS.128
-# of column factors per column shared by the thread's 4 rows.
-OWN_SLOTS = {6: 8.0 + 0.5 + 0.25, 4: 7.0 + 0.5 + 0.25}
+# Issue slots per pair of the binary32 kernel's factorised sequence (segments
+# whose rows and columns are narrow, >99.8% of the evaluated pairs here): FADD u,
+# FMUL w, Horner He_r (FADD + r/2 - 1 FFMA), 2 FFMA for the 3-term coupling factor
+# (1 for the 2-term one, one slot less), FFMA accumulate, 4/16 for one Kahan step
+# per 16 terms, and one LDS.128 of column factors per column shared by 4 rows.
+OWN_SLOTS = {6: 8.0 + 0.25 + 0.25, 4: 7.0 + 0.25 + 0.25}
 # The algorithmic per-pair sequence the roofline counts (one MUFU ex2 per pair).
 ALGO_SLOTS = {6: 7.0, 4: 6.0}
 KERNEL_SOURCE = os.path.join(ROOT, "paper_1505_02100_gb300", "csrc", "kde_kernels.cu")
@@ -89,8 +89,9 @@ def parse():
                     help="requests of the served stream to replay (0: skip the serving leg)")
     ap.add_argument("--serve-loads", type=str, default="0.8",
                     help="comma-separated arrival rates as fractions of the measured FP32 capacity")
-    ap.add_argument("--serve-fp64", action="store_true",
-                    help="also serve the FP64 subset: requests with n <= 65536 plus 20 random ones")
+    ap.add_argument("--serve-fp64", choices=["no", "also", "only"], default="no",
+                    help="the FP64 subset (requests with n <= 65536 plus 20 random ones): "
+                         "also, or only (without the FP32 replays)")
     ap.add_argument("--out-json", type=str, default=None, help="also write the JSON line here")
     return ap.parse_args()
 
@@ -400,11 +401,15 @@ def serve_summary(got, xs, gold=None, keys=None):
     return out
 
 
-def serve_leg(kde, capacity: float, count: int, loads, with_fp64: bool):
+def serve_leg(kde, capacity: float, count: int, loads, fp64_mode: str, out_prefix=None):
     """The first `count` requests of the served stream (n log-uniform in [1000, 4194304],
     FP32 samples, Poisson arrivals at `load` x the measured FP32 capacity), replayed in
-    real time through the continuous-batching server, once per load; optionally the
-    FP64 subset (requests with n <= 65536 plus 20 random ones) at the first load."""
+    real time through the continuous-batching server, once per load (FP32 path).
+    fp64_mode "also" / "only": the FP64 subset as well / alone -- the requests with
+    n <= 65536 plus 20 random ones, arriving at the first load's arrival times, served
+    in FP64; its FP32 figures are those requests' figures from the FP32 replay at that
+    load.  With `out_prefix`, every replay's summary and per-request records are written
+    as soon as it ends."""
     import numpy as np
 
     import synthdata
@@ -415,32 +420,53 @@ def serve_leg(kde, capacity: float, count: int, loads, with_fp64: bool):
     e_pairs = (hi * hi - lo * lo) / (2.0 * math.log(hi / lo))     # E[n^2] ~ E[n(n-1)], log-uniform n
     gold = golden("serve")
     out = {"sample": f"first {count} of the seeded 10000-request stream", "fp32": {}}
+
+    def dump(tag, summary, got, idx):
+        if not out_prefix:
+            return
+        with open(f"{out_prefix}.{tag}.json", "w") as f:
+            json.dump({"summary": summary,
+                       "requests": [{"index": int(specs[k].index), "n": int(specs[k].n),
+                                     "latency_ms": (tm["t_done_ns"] - tm["t_submit_ns"]) / 1e6,
+                                     "status": int(res["status"]), "h": res["h"], "psi6": res["psi6"],
+                                     "psi4": res["psi4"], "skipped": int(tm["skipped6"] + tm["skipped4"])}
+                                    for k, (res, tm) in zip(idx, got)]}, f)
+
+    first = {}
     for load in loads:
         rate = load * capacity / e_pairs
         arrivals = synthdata.poisson_arrivals(count, rate)
+        if fp64_mode == "only":
+            if load == loads[0]:
+                first = {"got": None, "arrivals": arrivals, "rate": rate}
+            continue
         got = serve_replay(kde, specs, xs, arrivals, kde.KDE_FP32)
         s = serve_summary(got, xs, gold, keys)
         s.update({"load": load, "arrival_rate_per_s": rate})
         out["fp32"][f"load_{load:g}"] = s
-    if with_fp64:
+        dump(f"fp32_load{load:g}", s, got, range(count))
+        if load == loads[0]:
+            first = {"got": got, "arrivals": arrivals, "rate": rate}
+    if fp64_mode in ("also", "only"):
         small = [k for k, s in enumerate(specs) if s.n <= 65536]
         rng = np.random.default_rng(7)
         others = [k for k in range(len(specs)) if specs[k].n > 65536]
         pick = sorted(small + list(rng.choice(others, size=min(20, len(others)), replace=False)))
-        sub_specs = [specs[k] for k in pick]
         sub_xs = [xs[k] for k in pick]
         sub_keys = [keys[k] for k in pick]
-        # the subset arrives at the first load's rate, in stream order
-        rate = loads[0] * capacity / e_pairs
-        arrivals = synthdata.poisson_arrivals(count, rate)[pick]
+        arrivals = first["arrivals"][pick]
         arrivals = arrivals - arrivals[0]
-        got64 = serve_replay(kde, sub_specs, sub_xs, arrivals, kde.KDE_FP64)
+        got64 = serve_replay(kde, [specs[k] for k in pick], sub_xs, arrivals, kde.KDE_FP64)
         s64 = serve_summary(got64, sub_xs, gold, sub_keys)
-        got32 = serve_replay(kde, sub_specs, sub_xs, arrivals, kde.KDE_FP32)
-        s32 = serve_summary(got32, sub_xs, gold, sub_keys)
-        out["fp64_subset"] = {"requests": len(pick), "selection": "n <= 65536 plus 20 random requests "
-                              "(numpy default_rng(7)) of the replayed stream", "fp64": s64, "fp32": s32,
-                              "fp32_over_fp64_pair_evals_per_s": s32["pair_evals_per_s"] / s64["pair_evals_per_s"]}
+        s64.update({"load_of_arrivals": loads[0], "arrival_rate_per_s": first["rate"]})
+        dump(f"fp64_subset_load{loads[0]:g}", s64, got64, pick)
+        sub = {"requests": len(pick), "selection": "n <= 65536 plus 20 random requests "
+               "(numpy default_rng(7)) of the replayed stream, at their arrival times", "fp64": s64}
+        if first.get("got") is not None:
+            s32 = serve_summary([first["got"][k] for k in pick], sub_xs, gold, sub_keys)
+            sub["fp32_same_requests_in_the_fp32_replay"] = s32
+            sub["fp32_over_fp64_pair_evals_per_s"] = s32["pair_evals_per_s"] / s64["pair_evals_per_s"]
+        out["fp64_subset"] = sub
     return out
 
 
@@ -603,7 +629,8 @@ def run_ours(args, ws, rank, local):
         bim = bimodal_leg(kde, torch, dev, stream, flush, with_fp64=not args.no_fp64)
     if ws == 1 and args.serve_requests > 0:
         loads = [float(v) for v in args.serve_loads.split(",") if v]
-        serve = serve_leg(kde, value, args.serve_requests, loads, args.serve_fp64)
+        serve = serve_leg(kde, value, args.serve_requests, loads, args.serve_fp64,
+                          args.out_json[:-5] if args.out_json and args.out_json.endswith(".json") else args.out_json)
 
     if rank != 0:
         return

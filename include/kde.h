@@ -257,7 +257,7 @@ KDE_API kde_status kde_tile_config(kde_precision prec, int64_t n, int32_t* info)
  *           Device: asynchronous on `stream`.
  * Set-up: the first call on a device, with that device current, looks up the
  * scratch area's address once (cudaGetSymbolAddress) and caches it; make that
- * first call before any stream capture meant to contain later calls.
+ * first call before any stream capture.
  * Concurrency: one scratch area per device.  Calls from several host threads on
  * the same stream are serialised by a lock held while the call enqueues its
  * work; calls that overlap on the device (different streams) race on the area

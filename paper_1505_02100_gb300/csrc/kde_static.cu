@@ -14,7 +14,7 @@
 //
 // Set-up: the first call on a device (with that device current) looks up the
 // array's address with cudaGetSymbolAddress and caches it per device. Do that
-// first call before any stream capture that is meant to contain later calls.
+// first call before any stream capture.
 // Later calls only launch kernels and copy the result.
 //
 // Zero state: the init kernel of every call clears the two work counters of

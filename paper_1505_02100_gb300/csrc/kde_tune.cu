@@ -3,7 +3,9 @@
 // Every configuration (threads x rows per thread = tile side T) computes the
 // same functional; they differ in occupancy, instruction-level parallelism and
 // in how evenly a sample's tile pairs spread over the SMs, which depends on n.
-// kde_autotune times each configuration through the ordinary psi_r path, on
+// kde_autotune times each configuration through the ordinary psi_r path -- psi6 at
+// the normal-reference g1 plus psi4 at the normal-reference g2, the two pair
+// launches of one PLUGIN run, which share one configuration -- on
 // synthetic normal samples of n = 2^10, 2^12, ..., 2^18 with device-resident
 // input and output, and records the fastest per size class for the current
 // device (the built-in choice stays unless another is at least 3% faster).
@@ -118,9 +120,12 @@ extern "C" kde_status kde_autotune(kde_precision prec, int32_t* chosen, int cap)
     int best_cfg[kTuneBuckets];
     for (int b = 0; b < kTuneBuckets && st == KDE_OK; ++b) {
       const int64_t n = int64_t(1) << kTuneLog2[b];
-      // normal-reference g1 for sigma = 1 (Steps II-III)
+      // normal-reference pilots for sigma = 1: g1 from psi8 (Steps II-III), g2 from
+      // the normal psi6 = -15 / (16 sqrt(pi)) (the form of Step V)
       const double psi8 = 105.0 / (32.0 * std::sqrt(kPi));
       const double g = std::pow(30.0 / std::sqrt(2.0 * kPi) / (psi8 * static_cast<double>(n)), 1.0 / 9.0);
+      const double psi6 = 15.0 / (16.0 * std::sqrt(kPi));   // |psi6| of N(0, 1)
+      const double g4 = std::pow(6.0 / std::sqrt(2.0 * kPi) / (psi6 * static_cast<double>(n)), 1.0 / 7.0);
       std::vector<float> ms_cfg(static_cast<size_t>(count), 1e30f);
       for (int c = 0; c < count && st == KDE_OK; ++c) {
         t_tune_force_cfg = c;
@@ -128,6 +133,7 @@ extern "C" kde_status kde_autotune(kde_precision prec, int32_t* chosen, int cap)
         for (int rep = 0; rep < 4 && st == KDE_OK; ++rep) {   // first one warms up (and captures the graph)
           cu(cudaEventRecord(e0, s), "record");
           kde_status ps = kde_psi(xd, n, 6, g, prec, outd, s);
+          if (ps == KDE_OK) ps = kde_psi(xd, n, 4, g4, prec, outd, s);
           if (ps != KDE_OK) st = ps;
           cu(cudaEventRecord(e1, s), "record");
           cu(cudaEventSynchronize(e1), "sync");
