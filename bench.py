@@ -92,6 +92,8 @@ def parse():
     ap.add_argument("--serve-fp64", choices=["no", "also", "only"], default="no",
                     help="the FP64 subset (requests with n <= 65536 plus 20 random ones): "
                          "also, or only (without the FP32 replays)")
+    ap.add_argument("--serve-fp64-random", type=int, default=20,
+                    help="random requests with n > 65536 added to the FP64 subset")
     ap.add_argument("--out-json", type=str, default=None, help="also write the JSON line here")
     return ap.parse_args()
 
@@ -401,12 +403,13 @@ def serve_summary(got, xs, gold=None, keys=None):
     return out
 
 
-def serve_leg(kde, capacity: float, count: int, loads, fp64_mode: str, out_prefix=None):
+def serve_leg(kde, capacity: float, count: int, loads, fp64_mode: str, out_prefix=None,
+              fp64_random: int = 20):
     """The first `count` requests of the served stream (n log-uniform in [1000, 4194304],
     FP32 samples, Poisson arrivals at `load` x the measured FP32 capacity), replayed in
     real time through the continuous-batching server, once per load (FP32 path).
     fp64_mode "also" / "only": the FP64 subset as well / alone -- the requests with
-    n <= 65536 plus 20 random ones, arriving at the first load's arrival times, served
+    n <= 65536 plus `fp64_random` random ones, arriving at the first load's arrival times, served
     in FP64; its FP32 figures are those requests' figures from the FP32 replay at that
     load.  With `out_prefix`, every replay's summary and per-request records are written
     as soon as it ends."""
@@ -451,7 +454,8 @@ def serve_leg(kde, capacity: float, count: int, loads, fp64_mode: str, out_prefi
         small = [k for k, s in enumerate(specs) if s.n <= 65536]
         rng = np.random.default_rng(7)
         others = [k for k in range(len(specs)) if specs[k].n > 65536]
-        pick = sorted(small + list(rng.choice(others, size=min(20, len(others)), replace=False)))
+        extra = list(rng.choice(others, size=min(fp64_random, len(others)), replace=False)) if fp64_random > 0 else []
+        pick = sorted(small + extra)
         sub_xs = [xs[k] for k in pick]
         sub_keys = [keys[k] for k in pick]
         arrivals = first["arrivals"][pick]
@@ -460,7 +464,7 @@ def serve_leg(kde, capacity: float, count: int, loads, fp64_mode: str, out_prefi
         s64 = serve_summary(got64, sub_xs, gold, sub_keys)
         s64.update({"load_of_arrivals": loads[0], "arrival_rate_per_s": first["rate"]})
         dump(f"fp64_subset_load{loads[0]:g}", s64, got64, pick)
-        sub = {"requests": len(pick), "selection": "n <= 65536 plus 20 random requests "
+        sub = {"requests": len(pick), "selection": f"n <= 65536 plus {len(extra)} random requests "
                "(numpy default_rng(7)) of the replayed stream, at their arrival times", "fp64": s64}
         if first.get("got") is not None:
             s32 = serve_summary([first["got"][k] for k in pick], sub_xs, gold, sub_keys)
@@ -630,7 +634,8 @@ def run_ours(args, ws, rank, local):
     if ws == 1 and args.serve_requests > 0:
         loads = [float(v) for v in args.serve_loads.split(",") if v]
         serve = serve_leg(kde, value, args.serve_requests, loads, args.serve_fp64,
-                          args.out_json[:-5] if args.out_json and args.out_json.endswith(".json") else args.out_json)
+                          args.out_json[:-5] if args.out_json and args.out_json.endswith(".json") else args.out_json,
+                          args.serve_fp64_random)
 
     if rank != 0:
         return
@@ -702,6 +707,16 @@ def run_ours(args, ws, rank, local):
     if fp64:
         line["fp64"] = fp64
         line["fp32_over_fp64"] = value / fp64["value"]
+        # binary64 pair sequence on the factorised path: DADD u, DMUL w, 3 DFMA (He_6
+        # Horner), 4 DFMA (coupling to p^4/24), 1 DFMA (accumulate); bound by the FP64 pipe
+        fp64_ops = 10.0
+        fp64_peak = ws * sms * 2070e6 * rates_clk["fp64_fma_lanes_per_clk_sm"] / fp64_ops   # all ranks
+        line["fp64"]["roofline"] = {
+            "bound": "fp64", "unit": "Gpair-evals/s", "achieved": fp64["value"] / 1e9,
+            "peak": fp64_peak / 1e9, "frac": fp64["value"] / fp64_peak,
+            "peak_basis": (f"{sms} SMs x 2070 MHz x measured FP64 FMA "
+                           f"{rates_clk['fp64_fma_lanes_per_clk_sm']:.2f} lanes/clk/SM / {fp64_ops:g} "
+                           "binary64 operations per pair (psi6 sequence; psi4 has one fewer)")}
     if batch:
         line["batch"] = batch
     if serve:
