@@ -60,10 +60,11 @@ RESULT_FIELDS = ("psi6", "psi4", "h")
 
 # Issue slots per pair of the binary32 kernel's factorised sequence (segments
 # whose rows and columns are narrow, >99.8% of the evaluated pairs here): FADD u,
-# FMUL w, Horner He_r (FADD + r/2 - 1 FFMA), 2 FFMA for the 3-term coupling factor
-# (1 for the 2-term one, one slot less), FFMA accumulate, 4/16 for one Kahan step
-# per 16 terms, and one LDS.128 of column factors per column shared by 4 rows.
-OWN_SLOTS = {6: 8.0 + 0.25 + 0.25, 4: 7.0 + 0.25 + 0.25}
+# He_r straight from u in t = u^2 - (r - 1) (r/2 FFMA), 2 FFMA for the 3-term
+# coupling factor (1 for the 2-term one, one slot less), FFMA accumulate, 4/16 for
+# one Kahan step per 16 terms, and one LDS.128 of column factors per column shared
+# by 4 rows.
+OWN_SLOTS = {6: 7.0 + 0.25 + 0.25, 4: 6.0 + 0.25 + 0.25}
 # The algorithmic per-pair sequence the roofline counts (one MUFU ex2 per pair).
 ALGO_SLOTS = {6: 7.0, 4: 6.0}
 KERNEL_SOURCE = os.path.join(ROOT, "paper_1505_02100_gb300", "csrc", "kde_kernels.cu")

@@ -212,9 +212,34 @@ void build_plan(BatchPlan& P, int prec, int mode, int x_f32, const int64_t* ns, 
   h = fnv(h, &m, sizeof m);
   h = fnv(h, &g_fixed, sizeof g_fixed);
   h = fnv(h, ns, sizeof(int64_t) * static_cast<size_t>(m));
-  for (const Group& g : P.groups) h = fnv(h, &g.cfg, sizeof g.cfg);
+  for (const SampleDesc& d : P.desc) h = fnv(h, &d.cfg, sizeof d.cfg);
   P.key = h;
 }
+
+// What build_plan's result depends on: its arguments and each sample's tile
+// configuration (the autotuner or KDE_*_TILE_CONFIG may change that between
+// calls).  The device is fixed per workspace.
+struct PlanArgs {
+  int prec = -1, mode = 0, x_f32 = 0, stages = 0;
+  double g_fixed = 0.0;
+  std::vector<int64_t> ns;
+  std::vector<int> cfgs;
+
+  void set(int prec_, int mode_, int x_f32_, const int64_t* ns_, int64_t m, double g_, int stages_) {
+    prec = prec_;
+    mode = mode_;
+    x_f32 = x_f32_;
+    stages = stages_;
+    g_fixed = g_;
+    ns.assign(ns_, ns_ + m);
+    cfgs.resize(static_cast<size_t>(m));
+    for (int64_t k = 0; k < m; ++k) cfgs[k] = choose_config(prec_, ns_[k]);
+  }
+  bool operator==(const PlanArgs& o) const {
+    return prec == o.prec && mode == o.mode && x_f32 == o.x_f32 && stages == o.stages &&
+           std::memcmp(&g_fixed, &o.g_fixed, sizeof g_fixed) == 0 && ns == o.ns && cfgs == o.cfgs;
+  }
+};
 
 // ---------------------------------------------------------------------------
 // workspaces
@@ -241,6 +266,10 @@ struct Workspace {
   int64_t last_m = 0;      // samples of the last run on this workspace
   cudaEvent_t prof[5] = {};   // before init, after prescale r=6, after pairs r=6, after prescale r=4, after pairs r=4
   bool prof_valid = false;
+  // The plan of the last call and the arguments it was built from (plan_for).
+  BatchPlan plan;
+  PlanArgs plan_args;
+  bool plan_set = false;
 
   void drop_graphs() {
     for (auto& kv : graphs) cudaGraphExecDestroy(kv.second.exec);
@@ -262,6 +291,7 @@ struct Workspace {
     }
     prof_valid = false;
     meta_key = 0;
+    plan_set = false;
   }
 };
 
@@ -329,6 +359,23 @@ kde_status ensure(Workspace& W, DevBuf& b, size_t bytes) {
   W.drop_graphs();
   W.meta_key = 0;
   return KDE_OK;
+}
+
+// The plan for these arguments, built only when they differ from the last
+// call's on this workspace.  Building it is O(tile pairs) host work -- the
+// work-list of 524,800 items at n = 2^20, sorted by cost, ~10 ms -- during which
+// the GPU would idle between back-to-back calls.  Call with W.mu held; the
+// reference stays valid until the next plan_for on W.
+const BatchPlan& plan_for(Workspace& W, int prec, int mode, int x_f32, const int64_t* ns, int64_t m,
+                          double g_fixed, int stages = 2) {
+  PlanArgs a;
+  a.set(prec, mode, x_f32, ns, m, g_fixed, stages);
+  if (!W.plan_set || !(a == W.plan_args)) {
+    build_plan(W.plan, prec, mode, x_f32, ns, m, g_fixed, stages);
+    W.plan_args = std::move(a);
+    W.plan_set = true;
+  }
+  return W.plan;
 }
 
 kde_status reserve(Workspace& W, const BatchPlan& P) {
@@ -520,8 +567,7 @@ kde_status plugin_one(const void* x, int x_f32, int64_t n, kde_precision prec, k
   kde_status st = get_workspace(s, &W);
   if (st != KDE_OK) return st;
   std::lock_guard<std::mutex> lk(W->mu);
-  BatchPlan P;
-  build_plan(P, prec, kPlugin, x_f32, &n, 1, 0.0);
+  const BatchPlan& P = plan_for(*W, prec, kPlugin, x_f32, &n, 1, 0.0);
   if ((st = run_plan(*W, P, x, is_device_ptr(x), s)) != KDE_OK) return st;
   const bool out_dev = is_device_ptr(out);
   if ((st = copy_results(*W, 1, out, out_dev, s)) != KDE_OK) return st;
@@ -545,8 +591,7 @@ kde_status plugin_stages_one(const double* x, int64_t n, int stages, kde_precisi
   kde_status st = get_workspace(s, &W);
   if (st != KDE_OK) return st;
   std::lock_guard<std::mutex> lk(W->mu);
-  BatchPlan P;
-  build_plan(P, prec, kPlugin, 0, &n, 1, 0.0, stages);
+  const BatchPlan& P = plan_for(*W, prec, kPlugin, 0, &n, 1, 0.0, stages);
   if ((st = run_plan(*W, P, x, is_device_ptr(x), s)) != KDE_OK) return st;
   const bool out_dev = is_device_ptr(out);
   const auto* src = &static_cast<const SampleState*>(W->state.p)->sres;
@@ -558,18 +603,15 @@ kde_status plugin_stages_one(const double* x, int64_t n, int stages, kde_precisi
   return KDE_OK;
 }
 
-kde_status psi_run(const double* x, int64_t n, int r, double g, kde_precision prec, Workspace** Wout,
-                   cudaStream_t s, BatchPlan& P) {
+kde_status psi_check(const double* x, int64_t n, int r, double g, kde_precision prec, Workspace** Wout,
+                     cudaStream_t s) {
   if (!x) return set_err(KDE_ERR_INVALID, "null pointer");
   if (n < 2) return set_err(KDE_ERR_INVALID, "n < 2");
   if (r != 4 && r != 6 && r != 8 && r != 10) return set_err(KDE_ERR_INVALID, "r must be 4, 6, 8 or 10");
   if (!(g > 0) || !std::isfinite(g)) return set_err(KDE_ERR_INVALID, "g must be finite and > 0");
   if (prec != KDE_FP32 && prec != KDE_FP64 && prec != KDE_Q32) return set_err(KDE_ERR_INVALID, "bad precision");
   if (prec == KDE_Q32 && r > 6) return set_err(KDE_ERR_INVALID, "KDE_Q32 evaluates psi_4 and psi_6 only");
-  kde_status st = get_workspace(s, Wout);
-  if (st != KDE_OK) return st;
-  build_plan(P, prec, r, 0, &n, 1, g);
-  return KDE_OK;
+  return get_workspace(s, Wout);
 }
 
 }  // namespace kde
@@ -583,10 +625,10 @@ kde_status kde_psi(const double* x, int64_t n, int r, double g, kde_precision pr
   if (!out) return set_err(KDE_ERR_INVALID, "null pointer");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   Workspace* W = nullptr;
-  BatchPlan P;
-  kde_status st = psi_run(x, n, r, g, prec, &W, s, P);
+  kde_status st = psi_check(x, n, r, g, prec, &W, s);
   if (st != KDE_OK) return st;
   std::lock_guard<std::mutex> lk(W->mu);
+  const BatchPlan& P = plan_for(*W, prec, r, 0, &n, 1, g);
   if ((st = run_plan(*W, P, x, is_device_ptr(x), s)) != KDE_OK) return st;
   const auto* dst = static_cast<const SampleState*>(W->state.p);
   if (is_device_ptr(out)) {
@@ -605,9 +647,10 @@ kde_status kde_psi_slots(const double* x, int64_t n, int r, double g, kde_precis
                          double* slots, int64_t cap, int64_t* info) {
   if (!info) return set_err(KDE_ERR_INVALID, "null info");
   Workspace* W = nullptr;
-  BatchPlan P;
-  kde_status st = psi_run(x, n, r, g, prec, &W, nullptr, P);
+  kde_status st = psi_check(x, n, r, g, prec, &W, nullptr);
   if (st != KDE_OK) return st;
+  std::lock_guard<std::mutex> lk(W->mu);
+  const BatchPlan& P = plan_for(*W, prec, r, 0, &n, 1, g);
   const SampleDesc& d = P.desc[0];
   info[0] = pair_config(prec, P.groups[0].cfg).tile();
   info[1] = d.chunk;
@@ -615,7 +658,6 @@ kde_status kde_psi_slots(const double* x, int64_t n, int r, double g, kde_precis
   info[3] = d.nchunks;
   if (!slots) return KDE_OK;
   if (cap < d.nchunks) return set_err(KDE_ERR_INVALID, "slot capacity too small");
-  std::lock_guard<std::mutex> lk(W->mu);
   if ((st = run_plan(*W, P, x, is_device_ptr(x), nullptr)) != KDE_OK) return st;
   KDE_CU(cudaMemcpy(slots, W->slots.p, static_cast<size_t>(d.nchunks) * sizeof(double), cudaMemcpyDeviceToHost));
   return KDE_OK;
@@ -650,8 +692,7 @@ kde_status kde_plugin_h_batch(const double* x_packed, const int64_t* offsets, in
   kde_status st = get_workspace(s, &W);
   if (st != KDE_OK) return st;
   std::lock_guard<std::mutex> lk(W->mu);
-  BatchPlan P;
-  build_plan(P, prec, kPlugin, 0, ns.data(), m, 0.0);
+  const BatchPlan& P = plan_for(*W, prec, kPlugin, 0, ns.data(), m, 0.0);
   if ((st = run_plan(*W, P, x_packed, is_device_ptr(x_packed), s)) != KDE_OK) return st;
   return copy_results(*W, m, out, is_device_ptr(out), s);
 }

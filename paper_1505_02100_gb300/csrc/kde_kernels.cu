@@ -465,8 +465,9 @@ __host__ __device__ constexpr double he_at_zero() {
 // = kCHi + c_lo split into two binary32 values.  k = round(w kCHi) by the
 // 1.5 * 2^23 rounding trick, f = k - w kCHi in [-1/2, 1/2] from one FFMA (the
 // exact value of a 48-bit product minus an integer, rounded once), 2^f by a
-// degree-8 minimax polynomial (relative error 1.1e-12, fitted by Remez
-// exchange, p(0) = 1 exactly), and k goes straight into the exponent field.
+// degree-8 minimax polynomial (a Remez fit, p(0) = 1 exactly; with its
+// coefficients in binary32 its relative error is 1.3e-9, from float32(ln 2)),
+// and k goes straight into the exponent field.
 // That is exp(-u^2/2) scaled by 2^(-w c_lo) = 1 - w c_lo ln 2 + O(1e-12).
 //
 // The c_lo factor is not applied to f or to the term: there it would be a
@@ -642,6 +643,28 @@ __device__ __forceinline__ float hermite_w(float w) {
                    w, -945.0f);
 }
 
+// He_r straight from u for r = 4 and 6.  In t = u^2 - (r - 1) the second-highest
+// power of He_r(u) vanishes (r - 1 is the mean of its roots in u^2):
+//   He_4 = t^2 - 6,          t = u^2 - 3,
+//   He_6 = (t^2 - 30) t - 40, t = u^2 - 5,
+// so the square folds into the first FMA, one operation fewer than Horner in
+// w = u^2.  t is rounded once; near u = 0 its error (half an ulp of r - 1), times
+// He_r's slope there, is about 1e-6 of the term -- an unbiased rounding like the
+// others, which the pair sums average out.  Higher orders keep the Horner form in
+// w, where the same shift would be amplified 30-45 times more.
+template <int RORD>
+__device__ __forceinline__ float hermite_u(float u) {
+  if (RORD == 4) {
+    const float t = __fmaf_rn(u, u, -3.0f);
+    return __fmaf_rn(t, t, -6.0f);
+  }
+  if (RORD == 6) {
+    const float t = __fmaf_rn(u, u, -5.0f);
+    return __fmaf_rn(__fmaf_rn(t, t, -30.0f), t, -40.0f);
+  }
+  return hermite_w<RORD>(__fmul_rn(u, u));
+}
+
 // The column factors of one segment of `width` columns: fac[j] = (beta_j, C_j,
 // C_j beta_j, C_j beta_j^2) with C_j = exp(beta_j (Delta - beta_j/2) - Delta^2/2);
 // the exponent is formed as a double-float (Delta^2 split exactly by an FMA).
@@ -688,8 +711,7 @@ __device__ __forceinline__ void tile_pass_fac(const float4* __restrict__ fac, in
       const float4 f = fac[jj + q];
 #pragma unroll
       for (int r = 0; r < ROWS; ++r) {
-        const float u = __fsub_rn(ap[r], f.x);
-        const float h = hermite_w<RORD>(__fmul_rn(u, u));
+        const float h = hermite_u<RORD>(__fsub_rn(ap[r], f.x));
         float e = __fmaf_rn(al[r], f.z, f.y);
         if (K == 2) e = __fmaf_rn(ah[r], f.w, e);
         grp[r] = __fmaf_rn(h, e, grp[r]);
