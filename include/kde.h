@@ -17,7 +17,10 @@
  *    asks the CUDA runtime which, copies host data itself, and never keeps a
  *    caller pointer after the call returns (the server copies at submit).
  *  - The caller owns every buffer it passes.  The library owns its own device
- *    workspaces and frees them in kde_shutdown() or at process exit.
+ *    workspaces and frees them in kde_shutdown() or at process exit.  Each
+ *    (device, stream) has one workspace; it keeps the plan of its last call
+ *    (tiling and work-list) and a CUDA graph per plan, so a repeated call of the
+ *    same shape does no host planning and replays one graph.
  *  - `stream` is a cudaStream_t (NULL = the legacy default stream).  When every
  *    output pointer is device memory the call only enqueues work on `stream`
  *    and returns; the status words in the device outputs are then the result.
