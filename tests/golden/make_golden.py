@@ -9,6 +9,7 @@ it writes and compare the GPU path against them field by field.
     python tests/golden/make_golden.py batch          # the 512-sample batch, n <= 65536
     python tests/golden/make_golden.py batch --all    # ... and the larger samples too
     python tests/golden/make_golden.py serve          # served stream, first 1000 requests, n <= 65536
+    python tests/golden/make_golden.py serve_mid      # ... and those with 65536 < n <= 262144
 
 Each line is written as soon as its sample is done, and a rerun skips the samples
 already present, so a long run can be stopped and resumed.  The oracle's result
@@ -36,6 +37,7 @@ FILES = {
     "large": "plugin_large_n1048576.txt",
     "batch": "plugin_batch512_seed6.txt",
     "serve": "plugin_serve1000_seed7_small.txt",
+    "serve_mid": "plugin_serve1000_seed7_mid.txt",
 }
 
 DESCRIPTIONS = {
@@ -48,6 +50,9 @@ DESCRIPTIONS = {
     "serve": ("Oracle results for the served stream (synthdata.server_specs(10000, 7, 1000,\n"
               "4194304)), binary32 samples widened to binary64; key = request index.  The\n"
               "first 1000 requests with n <= 65536."),
+    "serve_mid": ("Oracle results for the served stream (synthdata.server_specs(10000, 7, 1000,\n"
+                  "4194304)), binary32 samples widened to binary64; key = request index.  The\n"
+                  "first 1000 requests with 65536 < n <= 262144."),
 }
 
 
@@ -69,9 +74,10 @@ def _jobs(kind: str, include_all: bool):
         for spec in synthdata.batch_specs(512, 6, 256, 262144):
             if include_all or spec.n <= 65536:
                 yield str(spec.index), (lambda s=spec: synthdata.sample_from_spec(s))
-    elif kind == "serve":
+    elif kind in ("serve", "serve_mid"):
+        lo, hi = (0, 65536) if kind == "serve" else (65536, 262144)
         for spec in synthdata.server_specs(10000, 7, 1000, 4194304)[:1000]:
-            if spec.n <= 65536:
+            if lo < spec.n <= hi:
                 yield str(spec.index), (lambda s=spec: synthdata.sample_from_spec(s, np.float32)
                                         .astype(np.float64))
     else:
@@ -105,8 +111,8 @@ def main() -> None:
               f"{time.time() - t0:.1f}s", flush=True)
 
 
-def load(kind: str) -> dict[str, dict]:
-    """Parse a golden file into {key: {"n", "status", field: value}}."""
+def load_file(kind: str) -> dict[str, dict]:
+    """Parse one golden file into {key: {"n", "status", field: value}}."""
     out: dict[str, dict] = {}
     with open(os.path.join(_HERE, FILES[kind])) as f:
         for line in f:
@@ -116,6 +122,15 @@ def load(kind: str) -> dict[str, dict]:
             rec = {"n": int(parts[1]), "status": int(parts[2])}
             rec.update({k: float(v) for k, v in zip(FIELDS, parts[3:])})
             out[parts[0]] = rec
+    return out
+
+
+def load(kind: str) -> dict[str, dict]:
+    """The stored values of a workload: "serve" is the served stream's two files
+    (n <= 65536, and 65536 < n <= 262144 where that file exists)."""
+    out = load_file(kind)
+    if kind == "serve" and os.path.exists(os.path.join(_HERE, FILES["serve_mid"])):
+        out.update(load_file("serve_mid"))
     return out
 
 
